@@ -1,0 +1,206 @@
+/*
+ * mdx.h - C ABI of the GB300 modal-synthesis library (libmdx.so).
+ *
+ * The library runs the per-time-step modal update of nonlinear strings,
+ * membranes and plates (Diaz & Sandler, "Fast Differentiable Modal
+ * Simulation of Non-linear Strings, Membranes, and Plates", DAFx25):
+ *
+ *   modal oscillators              Sec. 3.2, Eq. 12-14
+ *   Stormer-Verlet update          Sec. 3.2, Eq. 20-23
+ *     q^{n+1} = g q^n + p q^{n-1} + r (fext^n - fnl^n)
+ *   tension modulation (strings, membranes)        Sec. 3.1, Eq. 8
+ *     fnl_mu = tau' lambda_mu q_mu sum_nu lambda_nu q_nu^2
+ *   von Karman coupling (plates)   Sec. 3.1, Eq. 9, with C^s_pn = H^n_ps (Sec. 4.3.3)
+ *     eta_n = sum_pq H^n_pq q_p q_q,  fnl_s = sum_n kappa_n eta_n sum_p H^n_ps q_p
+ *   pickup                         y^n = sum_mu c_mu q^{n+1}_mu
+ *
+ * and its reverse-mode derivative (adjoint time loop with checkpoints).
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns an int status: MDX_OK (0) or one of MDX_ERR_*.
+ *     mdx_last_error() returns a thread-local message for the last failure.
+ *   - "device" pointers are CUDA global-memory addresses on the plan's
+ *     device; "host" pointers are ordinary CPU memory.  The caller owns every
+ *     buffer it passes; the library never frees caller memory and keeps no
+ *     reference to host arrays after a call returns.
+ *   - Work is enqueued asynchronously on the given cudaStream_t (passed as
+ *     void*, NULL = legacy default stream).  Device-side failures (non-finite
+ *     state, a synchronisation wait that gave up) are reported per instance in
+ *     the optional `status` array once the stream has reached that point.
+ *   - Modes of all instances are concatenated in plan order: instance i owns
+ *     modes [mode_offset(i), mode_offset(i) + n_phi(i)).
+ *   - Calls that share a plan share its scratch memory: do not run two calls
+ *     on the same plan concurrently on different streams.
+ */
+#ifndef MDX_H
+#define MDX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MDX_OK 0
+#define MDX_ERR_ARG 1          /* invalid argument (message names the instance / mode) */
+#define MDX_ERR_UNSTABLE 2     /* coefficients outside the scheme's stability region */
+#define MDX_ERR_NONFINITE 3    /* non-finite input or state */
+#define MDX_ERR_TIMEOUT 4      /* a bounded device-side wait gave up */
+#define MDX_ERR_CUDA 5         /* a CUDA runtime call failed */
+#define MDX_ERR_OOM 6          /* device allocation failed */
+#define MDX_ERR_UNSUPPORTED 7  /* size or feature outside this build's limits */
+
+#define MDX_KIND_TENSION 0     /* string (Kirchhoff-Carrier) or membrane (Berger) */
+#define MDX_KIND_PLATE 1       /* von Karman plate */
+
+#define MDX_MAX_PHI 1024       /* transverse modes per instance */
+#define MDX_MAX_PSI 1024       /* stress modes per instance */
+
+/*
+ * One simulated object, described by its modal coefficients (Sec. 3.2, Eq. 12).
+ * All arrays are host memory, read during mdx_plan_create only.
+ *   kind     MDX_KIND_TENSION or MDX_KIND_PLATE
+ *   n_phi    N, number of transverse modes, 1..MDX_MAX_PHI
+ *   n_psi    M, number of in-plane stress modes (plate; 0 = linear plate)
+ *   dt       sampling period T > 0 (s)
+ *   omega2   [N] squared angular frequencies omega_mu^2 > 0 (Eq. 13)
+ *   gamma    [N] damping rates gamma_mu >= 0 (Eq. 14)
+ *   b        [N] input weights: fext^n_mu = b_mu e^n
+ *   c        [N] pickup weights: y^n = sum c_mu q^{n+1}_mu
+ *   lambda   [N] Laplacian eigenvalues (tension kind; may be NULL for plates)
+ *   tau      tau' = tension-modulation coefficient / mass density (tension kind)
+ *   H        [M][N][N] coupling tensor H^k_ij (Eq. 10), FP32, symmetric in i, j
+ *   kappa    [M] kappa_k = E / (2 rho zeta_k^4) (Eq. 9)
+ *   dH       optional [M][N][N] FP32 direction tensor (e.g. dH/d aspect) for
+ *            mdx_grad's directional derivative <dL/dH, dH>; NULL if unused
+ * Stability: every mode needs omega_mu * dt < 2 (Eq. 20 is explicit);
+ * otherwise mdx_plan_create fails with MDX_ERR_UNSTABLE naming the mode.
+ */
+typedef struct mdx_instance {
+    int kind;
+    int n_phi;
+    int n_psi;
+    double dt;
+    const double *omega2;
+    const double *gamma;
+    const double *b;
+    const double *c;
+    const double *lambda;
+    double tau;
+    const float *H;
+    const double *kappa;
+    const float *dH;
+} mdx_instance;
+
+/* Plan options; zero-initialise for defaults. */
+typedef struct mdx_options {
+    int device;        /* CUDA device ordinal of the plan (default 0) */
+    int max_ctas;      /* cap on persistent CTAs for the plate kernel (0 = one per SM) */
+    int ring_stages;   /* TMA ring depth of the plate kernel (0 = default) */
+    int stage_bytes;   /* bytes per ring stage (0 = default; multiple of 16) */
+    int force_split;   /* >0: split every plate over at least this many CTAs (tests) */
+    int wait_limit;    /* >0: spin-iteration cap of device waits (tests); 0 = default */
+} mdx_options;
+
+typedef struct mdx_plan mdx_plan;
+
+/* Thread-local description of the last error of this thread (never NULL). */
+const char *mdx_last_error(void);
+
+/* Library version string. */
+const char *mdx_version(void);
+
+/*
+ * Build a plan: validates every instance, computes the FP32 difference-form
+ * coefficients (eps = 2 gamma T / (1 + gamma T), r omega^2, r = T^2/(1+gamma T),
+ * algebraically equal to Eq. 21-23), copies H into the device layout and
+ * builds the work assignment.  The plan owns all device memory it allocates.
+ *   out      receives the plan (set to NULL on failure)
+ *   inst     [n_inst] instance descriptions (host)
+ *   opts     options or NULL
+ * Errors: MDX_ERR_ARG, MDX_ERR_UNSTABLE, MDX_ERR_NONFINITE, MDX_ERR_UNSUPPORTED,
+ *         MDX_ERR_OOM, MDX_ERR_CUDA.
+ */
+int mdx_plan_create(mdx_plan **out, const mdx_instance *inst, int n_inst,
+                    const mdx_options *opts);
+
+/* Release every resource of the plan (synchronises its device first). */
+int mdx_plan_destroy(mdx_plan *plan);
+
+/* Plan geometry: number of instances, total modes, per-instance mode offset. */
+int mdx_plan_info(const mdx_plan *plan, int *n_inst, long *total_modes,
+                  long *mode_offset /* [n_inst] or NULL */);
+
+/* Bytes of the checkpoint buffer mdx_simulate writes for `steps` steps with
+ * checkpoint interval K (state before steps 0, K, 2K, ...). */
+size_t mdx_checkpoint_bytes(const mdx_plan *plan, int steps, int K);
+
+/*
+ * Run `steps` steps of Eq. 20 for every instance.
+ *   exc      device [n_inst][steps] FP32 excitation e^n (NULL = zero)
+ *   q0, qm1  device [total_modes] FP64 initial states q^0, q^{-1} (NULL = zero)
+ *   audio    device [n_inst][steps] FP32 output y^n (NULL = not written)
+ *   q_end, qm1_end  device [total_modes] FP64 final q^steps, q^{steps-1} (NULL = skip);
+ *            feeding them back as q0, qm1 continues the run (resume)
+ *   K, ckpt  checkpoint interval and device buffer of mdx_checkpoint_bytes
+ *            (ckpt NULL = none)
+ *   status   device [n_inst] int, written MDX_OK / MDX_ERR_NONFINITE /
+ *            MDX_ERR_TIMEOUT per instance (NULL = not written)
+ *   stream   cudaStream_t
+ */
+int mdx_simulate(mdx_plan *plan, const float *exc, const double *q0, const double *qm1,
+                 int steps, float *audio, double *q_end, double *qm1_end, int K,
+                 void *ckpt, int *status, void *stream);
+
+/* Gradient outputs of mdx_grad: device FP64 arrays, each optional (NULL). */
+typedef struct mdx_grads {
+    double *d_omega2;   /* [total_modes] dL/d omega^2 */
+    double *d_gamma;    /* [total_modes] dL/d gamma */
+    double *d_b;        /* [total_modes] dL/d b */
+    double *d_c;        /* [total_modes] dL/d c */
+    double *d_q0;       /* [total_modes] dL/d q^0 */
+    double *d_qm1;      /* [total_modes] dL/d q^{-1} */
+    double *d_tau;      /* [n_inst] dL/d tau' (tension instances; 0 for plates) */
+    double *d_kappa;    /* [total stress modes] dL/d kappa, plates in plan order */
+    double *d_dir;      /* [n_inst] <dL/dH, dH> for plates planned with dH (else 0) */
+} mdx_grads;
+
+/* Bytes of the workspace mdx_grad needs for (steps, K). */
+size_t mdx_grad_workspace_bytes(const mdx_plan *plan, int steps, int K);
+
+/*
+ * Reverse-mode derivative of a scalar loss L(y) through the whole time loop.
+ * Given dL/dy it runs the adjoint recursion backwards, segment by segment:
+ * each K-step segment is recomputed from the checkpoint mdx_simulate wrote
+ * (same arguments, same K), then swept in reverse.
+ *   exc, q0, qm1, steps  as passed to mdx_simulate
+ *   d_audio  device [n_inst][steps] FP32 dL/dy^n
+ *   K, ckpt  the checkpoint interval and buffer filled by mdx_simulate
+ *   work     device workspace of mdx_grad_workspace_bytes (caller-owned scratch)
+ *   out      gradient outputs (fields may be NULL)
+ *   status   as in mdx_simulate
+ */
+int mdx_grad(mdx_plan *plan, const float *exc, const double *q0, const double *qm1,
+             int steps, const float *d_audio, int K, const void *ckpt, void *work,
+             size_t work_bytes, const mdx_grads *out, int *status, void *stream);
+
+/*
+ * Host FP64 map from physical parameters to modal coefficients for one
+ * mode set (Sec. 3.2, Eq. 13-14):
+ *   omega2_mu = (D lambda_mu^2 + T0 lambda_mu) / rho,  gamma_mu = s0 + s1 omega2_mu
+ * and its vector-Jacobian product: given dL/domega2 and dL/dgamma, returns
+ * dL/dD, dL/dT0, dL/ds0, dL/ds1 and dL/dlambda (per mode, for geometry).
+ * lambda, omega2, gamma, d_omega2, d_gamma, d_lambda: host [n] arrays.
+ */
+int mdx_coeffs_from_physics(int n, const double *lambda, double D, double T0, double rho,
+                            double s0, double s1, double *omega2, double *gamma);
+int mdx_coeffs_vjp(int n, const double *lambda, double D, double T0, double rho, double s0,
+                   double s1, const double *d_omega2, const double *d_gamma, double *dD,
+                   double *dT0, double *ds0, double *ds1, double *d_lambda);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MDX_H */
