@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""Benchmark of the per-time-step modal update: forward + adjoint of a batch of
+von Karman plates (Sec. 3.1, Eq. 9; Sec. 3.2, Eq. 20), with the
+multi-resolution log-STFT loss of Sec. 4.3.1 (Eq. 24) between them.
+
+Workload (per GPU): 64 simply supported steel plates, N_phi = 200 transverse
+and N_psi = 50 stress modes, tension, stiffness, aspect ratio and damping of
+each plate drawn log-uniform within +-0.3 decade of a target plate; 0.5 s at
+44.1 kHz (22 050 steps); loss against the target plate's audio; gradients
+with respect to omega^2, gamma, kappa and the aspect direction through the
+checkpointed adjoint (checkpoint interval K).
+
+One bench step = forward (with checkpoints) + loss + adjoint sweep.
+value = plate mode-steps per second = n_gpus * 64 * 200 * 22050 / step time.
+
+  python bench.py [--gpus N --steps K --warmup W]      # this library
+  python bench.py --impl reference                     # FP64 CPU oracle on host cores
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "plate mode-steps/s fwd+adjoint at ≤1e-5 rel err vs FP64; % of roofline"
+UNIT = "mode-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-inst", type=int, default=64)
+    ap.add_argument("--n-phi", type=int, default=200)
+    ap.add_argument("--n-psi", type=int, default=50)
+    ap.add_argument("--sim-steps", type=int, default=22050)
+    ap.add_argument("--K", type=int, default=1024)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workers", type=int, default=0)
+    return ap.parse_args()
+
+
+def workload_name(a):
+    return (f"adjoint{a.n_inst}_plate{a.n_phi}x{a.n_psi}_{a.sim_steps}steps_K{a.K}")
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------- inputs
+
+def _prepare_one(args):
+    inst, fs, steps, want_dir = args
+    from paper_2505_05940_gb300 import physics
+    return physics.prepare(inst, fs, steps, want_aspect_derivative=want_dir)
+
+
+def prepare_inputs(a, rank):
+    """Seeded target + initial guesses, prepared in a spawn process pool
+    (coupling tensors and their aspect derivatives are FP64 host work)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    from paper_2505_05940_gb300 import workloads as W
+    tgt, inits = W.adjoint_plates(seed=rank, n_inst=a.n_inst, n_phi=a.n_phi, n_psi=a.n_psi,
+                                  steps=a.sim_steps)
+    jobs = [(tgt.instances[0], tgt.fs, tgt.steps, False)]
+    jobs += [(i, inits.fs, inits.steps, True) for i in inits.instances]
+    workers = a.workers or max(1, min(len(jobs), (os.cpu_count() or 2)))
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        out = list(ex.map(_prepare_one, jobs))
+    return out[0], out[1:], inits
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- CPU oracle
+
+def oracle_sample(a, n_threads, sample_steps):
+    """FP64 oracle forward + adjoint (with dL/dH) of one plate per thread on a
+    bounded number of steps; returns (mode-steps/s, threads, description)."""
+    import oracle
+    from oracle import coupling_oracle as CO
+    from oracle import physics_oracle as PO
+    from paper_2505_05940_gb300 import workloads as W
+    _, inits = W.adjoint_plates(seed=0, n_inst=max(n_threads, 1), n_phi=a.n_phi,
+                                n_psi=a.n_psi, steps=sample_steps)
+    ois = [PO.build_instance(inits.instances[0], inits.fs, sample_steps,
+                             coupling=CO.oracle_coupling)]
+    for _ in range(1, n_threads):
+        ois.append(ois[0])
+    rng = np.random.default_rng(0)
+    ybar = rng.normal(size=sample_steps)
+    oracle.lib()
+
+    def work(oi):
+        oracle.adjoint(oi, ybar, want_dH=True)   # runs the forward (trajectory) then the reverse
+
+    ths = [threading.Thread(target=work, args=(o,)) for o in ois]
+    t0 = time.perf_counter()
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    dt = time.perf_counter() - t0
+    value = n_threads * ois[0].N * sample_steps / dt
+    desc = (f"{n_threads} thread(s) x one {ois[0].N}x{ois[0].M} plate x {sample_steps} steps "
+            f"forward+adjoint in FP64 (the oracle as it stands), {dt:.1f} s wall")
+    return value, n_threads, desc
+
+
+def reference_arm(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    per = []
+    for _ in range(a.warmup):
+        oracle_sample(a, cores, 50)
+    for _ in range(a.steps):
+        v, c, desc = oracle_sample(a, cores, 200)
+        per.append(v)
+    value = float(np.median(per))
+    ms = a.n_inst * a.n_phi * a.sim_steps / value * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload_name(a), "instances": a.n_inst,
+                                             "n_phi": a.n_phi, "n_psi": a.n_psi,
+                                             "sim_steps": a.sim_steps, "K": a.K},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- main arm
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        reference_arm(a)
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    # host-side preparation before any CUDA use (spawned workers)
+    tgt_p, init_p, inits_wl = prepare_inputs(a, rank)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2505_05940_gb300 import losses, modal
+    if world > 1:
+        dist.init_process_group("nccl", rank=rank, world_size=world)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    # target audio (outside the timed region)
+    tsim = modal.Simulator([tgt_p], device=str(dev))
+    target = tsim.simulate(a.sim_steps)["audio"].expand(a.n_inst, -1).contiguous()
+    sim = modal.Simulator(init_p, device=str(dev))
+    nseg = math.ceil(a.sim_steps / a.K)
+
+    def step():
+        for t in (sim.omega2, sim.gamma, sim.b, sim.c, sim.tau, sim.kappa, sim.q0, sim.qm1,
+                  sim.direction):
+            t.grad = None
+        audio = modal.simulate_autograd(sim, a.sim_steps, K=a.K)
+        loss = losses.multires_log_stft(audio, target).sum()
+        loss.backward()
+        return loss
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    sim.plan.set_profiling(True)
+    sim.plan.reset_stats()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(a.steps):
+            loss = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    t_local = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    ms_total = float(t_local.item())
+    ms_step = ms_total / a.steps
+    units = world * a.n_inst * a.n_phi * a.sim_steps
+    value = units / (ms_step * 1e-3)
+    # roofline of the dominant kernel (plate kernel: forward, recompute, reverse launches)
+    stats = {w: sim.plan.kernel_stats(w) for w in (0, 1, 2)}
+    sim.plan.set_profiling(False)
+    peak, peak_kind = load_peaks()
+    tot_ms = sum(s[1] for s in stats.values())
+    dom = max(stats, key=lambda w: stats[w][1])
+    n_l, d_ms, d_bytes = stats[dom]
+    achieved = (d_bytes / n_l) / ((d_ms / n_l) * 1e-3) / 1e9 if n_l else 0.0
+    names = {0: "plate_kernel<1> forward", 1: "plate_kernel<1> recompute",
+             2: "plate_kernel<2> reverse"}
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": names[dom], "peak_source": f"{peak_kind} hbm_gbs",
+                "kernel_share_of_step": tot_ms / ms_total if ms_total else None,
+                "per_launch_ms": d_ms / max(n_l, 1),
+                "per_launch_algorithmic_bytes": d_bytes / max(n_l, 1)}
+    roofline["all_plate_kernels"] = {
+        names[w]: {"launches": s[0], "ms": s[1],
+                   "GB/s": (s[2] / (s[1] * 1e-3) / 1e9) if s[1] else None}
+        for w, s in stats.items()}
+    # end-to-end through the public API with host buffers
+    e2e = None
+    if not a.no_e2e:
+        exc_host = sim.exc.cpu().pin_memory()
+        tgt_host = target.cpu().pin_memory()
+        out_keys = ("omega2", "gamma", "kappa", "direction")
+        h2d = exc_host.numel() * 4 + tgt_host.numel() * 4
+        d2h = 8 + sum(getattr(sim, k).numel() * 8 for k in out_keys)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            exc_d = exc_host.to(dev, non_blocking=True)
+            tgt_d = tgt_host.to(dev, non_blocking=True)
+            sim.exc = exc_d
+            for t in (sim.omega2, sim.gamma, sim.b, sim.c, sim.tau, sim.kappa, sim.q0,
+                      sim.qm1, sim.direction):
+                t.grad = None
+            audio = modal.simulate_autograd(sim, a.sim_steps, K=a.K)
+            loss = losses.multires_log_stft(audio, tgt_d).sum()
+            loss.backward()
+            res = [loss.detach().cpu()] + [getattr(sim, k).grad.cpu() for k in out_keys]
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / a.steps
+        e2e = {"value": units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+    cpu = None
+    if rank == 0 and not a.no_cpu_baseline:
+        v, cores, desc = oracle_sample(a, os.cpu_count() or 1, 200)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+    launches_per_step = 1 + 1 + 1 + 2 * nseg + 1   # init, forward, adjoint init, segments, epilogue
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": workload_name(a), "instances_per_gpu": a.n_inst,
+                           "n_phi": a.n_phi, "n_psi": a.n_psi, "sim_steps": a.sim_steps,
+                           "K": a.K, "loss": "multi-resolution log-STFT L1 (256/1024/4096)",
+                           "l2": "inputs larger than L2 (coupling tensors 512 MB per GPU)",
+                           "parallelism": f"instances sharded, {world} GPU(s), no collective"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches_per_step * a.steps, "clocks": clk.summary(),
+                "loss": float(loss.item())}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

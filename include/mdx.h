@@ -101,6 +101,9 @@ typedef struct mdx_options {
     int stage_bytes;   /* bytes per ring stage (0 = default; multiple of 16) */
     int force_split;   /* >0: split every plate over at least this many CTAs (tests) */
     int wait_limit;    /* >0: spin-iteration cap of device waits (tests); 0 = default */
+    int debug_flags;   /* bit 0: the second contributor of every shared plate withholds its
+                          arrival, so the other contributors' bounded waits run out and the
+                          call reports MDX_ERR_TIMEOUT (fault-path tests); 0 in normal use */
 } mdx_options;
 
 typedef struct mdx_plan mdx_plan;
@@ -184,6 +187,20 @@ size_t mdx_grad_workspace_bytes(const mdx_plan *plan, int steps, int K);
 int mdx_grad(mdx_plan *plan, const float *exc, const double *q0, const double *qm1,
              int steps, const float *d_audio, int K, const void *ckpt, void *work,
              size_t work_bytes, const mdx_grads *out, int *status, void *stream);
+
+/*
+ * Kernel timing (tracing).  When enabled, every plate-kernel launch of the
+ * plan is bracketed by CUDA events on its launch stream.  mdx_plan_kernel_stats
+ * synchronises those events and returns, for one launch class
+ * (0 = forward, 1 = checkpoint recompute, 2 = reverse sweep), the number of
+ * launches, their summed device time in ms and their summed algorithmic bytes
+ * (coupling-tensor bytes each launch must stream: one pass over H per step,
+ * plus one over dH per reverse step when a direction tensor is planned).
+ * mdx_plan_reset_stats clears the counters.  Off by default.
+ */
+int mdx_plan_set_profiling(mdx_plan *plan, int enable);
+int mdx_plan_kernel_stats(mdx_plan *plan, int which, long *launches, double *ms, double *bytes);
+int mdx_plan_reset_stats(mdx_plan *plan);
 
 /*
  * Host FP64 map from physical parameters to modal coefficients for one

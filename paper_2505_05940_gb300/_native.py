@@ -1,0 +1,267 @@
+"""ctypes binding of libmdx.so (include/mdx.h).
+
+Argument marshalling only: every step of the time loop runs in the library's
+CUDA kernels.  PyTorch supplies device memory and the current stream.  There
+is no fallback: if the compiled library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+KIND_TENSION = 0
+KIND_PLATE = 1
+
+_ERRORS = {
+    0: "MDX_OK", 1: "MDX_ERR_ARG", 2: "MDX_ERR_UNSTABLE", 3: "MDX_ERR_NONFINITE",
+    4: "MDX_ERR_TIMEOUT", 5: "MDX_ERR_CUDA", 6: "MDX_ERR_OOM", 7: "MDX_ERR_UNSUPPORTED",
+}
+
+EXPORTED = ("mdx_last_error", "mdx_version", "mdx_plan_create", "mdx_plan_destroy",
+            "mdx_plan_info", "mdx_checkpoint_bytes", "mdx_simulate", "mdx_grad_workspace_bytes",
+            "mdx_grad", "mdx_coeffs_from_physics", "mdx_coeffs_vjp", "mdx_plan_set_profiling",
+            "mdx_plan_kernel_stats", "mdx_plan_reset_stats")
+
+
+class MdxError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_F = ctypes.POINTER(ctypes.c_float)
+
+
+class Instance(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("n_phi", ctypes.c_int), ("n_psi", ctypes.c_int),
+                ("dt", ctypes.c_double), ("omega2", _D), ("gamma", _D), ("b", _D), ("c", _D),
+                ("lambda_", _D), ("tau", ctypes.c_double), ("H", _F), ("kappa", _D), ("dH", _F)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("max_ctas", ctypes.c_int),
+                ("ring_stages", ctypes.c_int), ("stage_bytes", ctypes.c_int),
+                ("force_split", ctypes.c_int), ("wait_limit", ctypes.c_int),
+                ("debug_flags", ctypes.c_int)]
+
+
+class Grads(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("d_omega2", "d_gamma", "d_b", "d_c", "d_q0",
+                                                "d_qm1", "d_tau", "d_kappa", "d_dir")]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libmdx.so (building it first when nvcc is available)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise OSError(f"libmdx.so not found at {path}; run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        vp, i32, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+        L.mdx_last_error.restype = ctypes.c_char_p
+        L.mdx_version.restype = ctypes.c_char_p
+        L.mdx_plan_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Instance), i32,
+                                      ctypes.POINTER(Options)]
+        L.mdx_plan_destroy.argtypes = [vp]
+        L.mdx_plan_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_long),
+                                    ctypes.POINTER(ctypes.c_long)]
+        L.mdx_checkpoint_bytes.argtypes = [vp, i32, i32]
+        L.mdx_checkpoint_bytes.restype = sz
+        L.mdx_simulate.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, i32, vp, vp, vp]
+        L.mdx_grad_workspace_bytes.argtypes = [vp, i32, i32]
+        L.mdx_grad_workspace_bytes.restype = sz
+        L.mdx_grad.argtypes = [vp, vp, vp, vp, i32, vp, i32, vp, vp, sz, ctypes.POINTER(Grads),
+                               vp, vp]
+        L.mdx_coeffs_from_physics.argtypes = [i32, _D, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                              _D, _D]
+        L.mdx_coeffs_vjp.argtypes = [i32, _D, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double, _D, _D, _D, _D, _D, _D, _D]
+        L.mdx_plan_set_profiling.argtypes = [vp, i32]
+        L.mdx_plan_reset_stats.argtypes = [vp]
+        L.mdx_plan_kernel_stats.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_long),
+                                            ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_double)]
+        for name in EXPORTED[2:]:
+            fn = getattr(L, name)
+            if fn.restype is None or fn.restype is ctypes.c_int:
+                fn.restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def check(rc):
+    if rc != 0:
+        raise MdxError(rc, load().mdx_last_error().decode())
+
+
+def _ptr(t):
+    """Device (or host) address of a torch tensor or numpy array, or None."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return ctypes.c_void_p(t.data_ptr())
+    return ctypes.c_void_p(t.ctypes.data)
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """A compiled set of instances on one device (owns the library plan).
+
+    `instances` is a list of dicts with keys kind ('tension' | 'plate'),
+    omega2, gamma, b, c (float64 arrays [N]), dt, and either lam, tau
+    (tension) or H [M][N][N] float32, kappa [M] (plate), optional dH.
+    """
+
+    def __init__(self, instances, device=0, max_ctas=0, ring_stages=0, stage_bytes=0,
+                 force_split=0, wait_limit=0, debug_flags=0):
+        L = load()
+        self._keep = []
+        arr = (Instance * len(instances))()
+        for i, d in enumerate(instances):
+            kind = KIND_PLATE if d["kind"] == "plate" else KIND_TENSION
+            N = int(len(d["omega2"]))
+            s = arr[i]
+            s.kind = kind
+            s.n_phi = N
+            s.dt = float(d["dt"])
+
+            def dptr(x):
+                a = np.ascontiguousarray(x, dtype=np.float64)
+                self._keep.append(a)
+                return a.ctypes.data_as(_D)
+
+            def fptr(x):
+                a = np.ascontiguousarray(x, dtype=np.float32)
+                self._keep.append(a)
+                return a.ctypes.data_as(_F)
+
+            s.omega2, s.gamma, s.b, s.c = (dptr(d[k]) for k in ("omega2", "gamma", "b", "c"))
+            if kind == KIND_TENSION:
+                s.lambda_ = dptr(d["lam"])
+                s.tau = float(d.get("tau", 0.0))
+                s.n_psi = 0
+            else:
+                H = d.get("H")
+                if H is not None and len(H) > 0:
+                    s.n_psi = int(H.shape[0])
+                    s.H = fptr(H)
+                    s.kappa = dptr(d["kappa"])
+                    if d.get("dH") is not None:
+                        s.dH = fptr(d["dH"])
+                else:
+                    s.n_psi = 0
+        opts = Options(device, max_ctas, ring_stages, stage_bytes, force_split, wait_limit,
+                       debug_flags)
+        h = ctypes.c_void_p()
+        check(L.mdx_plan_create(ctypes.byref(h), arr, len(instances), ctypes.byref(opts)))
+        self._h = h
+        self._keep = []
+        n = ctypes.c_int()
+        tm = ctypes.c_long()
+        check(L.mdx_plan_info(h, ctypes.byref(n), ctypes.byref(tm), None))
+        self.n_inst = n.value
+        self.total_modes = tm.value
+        offs = (ctypes.c_long * self.n_inst)()
+        check(L.mdx_plan_info(h, None, None, offs))
+        self.mode_offset = np.array(offs[:], dtype=np.int64)
+        self.n_modes = np.array([len(d["omega2"]) for d in instances], dtype=np.int64)
+        self.n_stress = np.array([0 if d["kind"] != "plate" or d.get("H") is None
+                                  else len(d["H"]) for d in instances], dtype=np.int64)
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().mdx_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ tracing
+    def set_profiling(self, enable=True):
+        check(load().mdx_plan_set_profiling(self._h, 1 if enable else 0))
+
+    def reset_stats(self):
+        check(load().mdx_plan_reset_stats(self._h))
+
+    def kernel_stats(self, which):
+        """which: 0 forward, 1 recompute, 2 reverse -> (launches, ms, bytes)."""
+        n = ctypes.c_long()
+        ms = ctypes.c_double()
+        by = ctypes.c_double()
+        check(load().mdx_plan_kernel_stats(self._h, which, ctypes.byref(n), ctypes.byref(ms),
+                                           ctypes.byref(by)))
+        return n.value, ms.value, by.value
+
+    # ------------------------------------------------------------------ calls
+    def checkpoint_bytes(self, steps, K):
+        return int(load().mdx_checkpoint_bytes(self._h, steps, K))
+
+    def workspace_bytes(self, steps, K):
+        return int(load().mdx_grad_workspace_bytes(self._h, steps, K))
+
+    def simulate(self, steps, exc=None, q0=None, qm1=None, K=0, ckpt=None, audio=None,
+                 q_end=None, qm1_end=None, status=None, stream=None):
+        """Raw call: every tensor argument is a CUDA tensor already allocated
+        by the caller (see include/mdx.h for shapes)."""
+        check(load().mdx_simulate(self._h, _ptr(exc), _ptr(q0), _ptr(qm1), int(steps),
+                                  _ptr(audio), _ptr(q_end), _ptr(qm1_end), int(K), _ptr(ckpt),
+                                  _ptr(status), _stream(stream)))
+
+    def grad(self, steps, d_audio, K, ckpt, work, exc=None, q0=None, qm1=None, out=None,
+             status=None, stream=None):
+        g = Grads()
+        if out:
+            for k, v in out.items():
+                setattr(g, k, _ptr(v).value if v is not None else None)
+        wb = work.numel() * work.element_size()
+        check(load().mdx_grad(self._h, _ptr(exc), _ptr(q0), _ptr(qm1), int(steps),
+                              _ptr(d_audio), int(K), _ptr(ckpt), _ptr(work), wb,
+                              ctypes.byref(g), _ptr(status), _stream(stream)))
+
+
+def coeffs_from_physics(lam, D, T0, rho, s0, s1):
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    w2 = np.zeros_like(lam)
+    gm = np.zeros_like(lam)
+    check(load().mdx_coeffs_from_physics(len(lam), lam.ctypes.data_as(_D), D, T0, rho, s0, s1,
+                                         w2.ctypes.data_as(_D), gm.ctypes.data_as(_D)))
+    return w2, gm
+
+
+def coeffs_vjp(lam, D, T0, rho, s0, s1, d_omega2, d_gamma):
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    dw = np.ascontiguousarray(d_omega2, dtype=np.float64)
+    dg = np.ascontiguousarray(d_gamma, dtype=np.float64)
+    out = [ctypes.c_double() for _ in range(4)]
+    dl = np.zeros_like(lam)
+    check(load().mdx_coeffs_vjp(len(lam), lam.ctypes.data_as(_D), D, T0, rho, s0, s1,
+                                dw.ctypes.data_as(_D), dg.ctypes.data_as(_D),
+                                *[ctypes.byref(o) for o in out], dl.ctypes.data_as(_D)))
+    return dict(D=out[0].value, T0=out[1].value, s0=out[2].value, s1=out[3].value, lam=dl)

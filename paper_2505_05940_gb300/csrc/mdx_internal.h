@@ -1,0 +1,186 @@
+// Internal layout of an mdx plan, shared by the host planner and the kernels.
+//
+// Modal state on the device uses the difference form of the Stormer-Verlet
+// update (Sec. 3.2, Eq. 20-23 rewritten exactly):
+//     v^{n+1} = v^n - eps v^n - (r omega^2) q^n + r (b e^n - fnl(q^n)),
+//     q^{n+1} = q^n + v^{n+1},
+// with v^n = q^n - q^{n-1}, eps = 2 gamma T / (1 + gamma T),
+// r = T^2 / (1 + gamma T).  q and v are carried as unevaluated FP32 pairs
+// (hi + lo, compensated addition) and r omega^2 as an FP32 pair: the per-step
+// increments are small against the values, and plain FP32 would accumulate
+// a phase drift of order 1e-5 over 1e4-1e5 steps.  The nonlinear force is
+// evaluated at q_hi.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace mdx {
+
+constexpr int kPlateThreads = 256;     // consumer threads of the plate kernel
+constexpr int kPlateWarps = kPlateThreads / 32;
+constexpr int kProducerWarps = 1;      // one warp issues the TMA bulk copies
+constexpr int kPlateBlock = kPlateThreads + 32 * kProducerWarps;
+constexpr int kStateArrays = 4;      // q_hi, q_lo, v_hi, v_lo
+constexpr int kMaxSpt = 4;             // modes per consumer thread (N_pad <= 1024)
+constexpr int kChunkK = 4;             // stress modes reduced together
+constexpr int kTensionWarpsPerBlock = 4;
+constexpr int kTensionMaxJ = 32;       // modes per lane (N <= 1024)
+
+enum KernelMode : int {
+    MODE_FORWARD = 0,   // simulate: writes audio / checkpoints / final state
+    MODE_RECOMPUTE = 1, // re-run one segment from a checkpoint, storing every state
+    MODE_REVERSE = 2,   // adjoint sweep over one stored segment
+};
+
+// Per-mode FP32 coefficients, concatenated over instances (struct of arrays).
+struct ModeCoef {
+    const float *eps;   // 2 gamma T / (1 + gamma T)
+    const float *rw2;   // r omega^2 (high part)
+    const float *rw2lo; // r omega^2 - rw2 (low part)
+    const float *r;     // T^2 / (1 + gamma T)
+    const float *b;     // input weight
+    const float *c;     // pickup weight
+    const float *lam;   // Laplacian eigenvalue (tension kind)
+};
+
+struct InstDesc {
+    int kind;           // MDX_KIND_TENSION / MDX_KIND_PLATE
+    int N;              // transverse modes
+    int M;              // stress modes (0 for tension / linear)
+    int Npad;           // row stride of H (multiple of 4 floats)
+    long long mode_off; // offset into per-mode arrays
+    long long H_off;    // float offset of H^0 (layout [M][N][Npad])
+    long long k_off;    // offset into per-stress-mode arrays (kappa, d_kappa)
+    float taup;         // tension coefficient / density
+    int n_contrib;      // plate: number of CTAs holding a part of the k range
+    long long part_off; // plate: first exchange slot (slots are [n_contrib][3][Npad])
+    int has_dir;        // plate: a direction tensor dH is present
+    long long dH_off;   // float offset of dH^0 (same layout as H)
+};
+
+// One contiguous range of stress modes of one plate, processed by one CTA.
+struct PlateItem {
+    int inst;
+    int k0, k1;         // stress modes [k0, k1)
+    int slot;           // this CTA's index among the instance's contributors
+    int owner;          // 1: this CTA writes audio / state / gradients of the instance
+    int smem_state;     // float offset of this item's state block in shared memory
+};
+
+// Shared-memory state block of one item (floats, each of length Npad).
+enum StateArr : int {
+    ST_QHI = 0, ST_QLO, ST_V, ST_VLO,  // forward / recompute state (reverse: a_hi, a_lo, mu)
+    ST_FLOC,                        // local partial force (forward) / J w (reverse)
+    ST_SRC0, ST_SRC1,               // right-hand sides of the H pass (reverse: q^n, w)
+    ST_FLOC2,                       // reverse: local partial force at q^n
+    ST_NARR
+};
+
+// Accumulators of the reverse sweep, per mode (compensated FP32 pairs).
+enum GradAcc : int {
+    GA_A = 0,   // sum a^{n+1} q^n
+    GA_V,       // sum a^{n+1} v^n
+    GA_F,       // sum a^{n+1} (b e^n - fnl^n)
+    GA_E,       // sum a^{n+1} e^n
+    GA_C,       // sum ybar^n q^{n+1}
+    GA_N
+};
+
+// Persistent adjoint state between segment launches (per mode):
+// a_hi, a_lo (adjoint a^{n+1}), mu = a^{n+1} - a^{n+2}.
+enum AdjArr : int { AD_HI = 0, AD_LO, AD_MU, AD_N };
+
+struct PlateParams {
+    const InstDesc *inst;
+    const PlateItem *items;
+    const int *cta_item_off;      // [gridDim+1]
+    ModeCoef coef;
+    const float *H;
+    const float *dH;
+    const float *kappa;           // [total stress modes]
+    int n_inst;
+    int steps;                    // steps of this launch
+    int n_begin;                  // global step index of the first step
+    int total_steps;              // steps of the whole simulate call (exc / audio row length)
+    int mode;                     // KernelMode
+    int stage_bytes;
+    int ring_stages;
+    int max_spt;
+    int smem_state_floats;
+    // forward I/O
+    const float *exc;             // [n_inst][total_steps]
+    float *audio;                 // [n_inst][total_steps]
+    float *state_io;              // [4][total_modes] q_hi, q_lo, v_hi, v_lo in / out
+    int ckpt_K;
+    float *ckpt;                  // [n_ckpt][4][total_modes]
+    float *seg_q;                 // recompute/reverse: [(steps+1)][total_modes] q_hi^n
+    float *seg_v;                 // recompute/reverse: [(steps+1)][total_modes] v^n
+    long long total_modes;
+    // reverse I/O
+    const float *ybar;            // [n_inst][total_steps]
+    float *adj;                   // [AD_N][total_modes]
+    float *gacc;                  // [GA_N][2][total_modes]
+    float *kacc;                  // [total stress modes][2] d kappa (Kahan pair)
+    float *diracc;                // [total stress modes][2] directional derivative per k (Kahan pair)
+    // synchronisation
+    float *part;                  // exchange slots, two parities of part_stride floats
+    long long part_stride;
+    unsigned *counters;           // [n_inst]
+    int *status;                  // [n_inst] or nullptr
+    int *abort_flag;
+    long long wait_limit;
+    int debug_flags;
+};
+
+struct TensionParams {
+    const InstDesc *inst;
+    const int *list;              // tension instance indices
+    int n_list;
+    ModeCoef coef;
+    int steps, n_begin, total_steps, mode;
+    const float *exc;
+    float *audio;
+    float *state_io;
+    int ckpt_K;
+    float *ckpt;
+    float *seg_q, *seg_v;
+    long long total_modes;
+    const float *ybar;
+    float *adj;
+    float *gacc;
+    float *tacc;                  // [n_inst][2] d tau' (Kahan sum, compensation)
+    int *status;
+};
+
+// Launchers (defined in the kernel translation units).
+size_t plate_smem_bytes(int ring_stages, int stage_bytes, int npad_max, int state_floats);
+cudaError_t launch_plate(const PlateParams &p, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_tension(const TensionParams &p, int max_n, cudaStream_t s);
+
+struct AuxInit {
+    const double *q0, *qm1;      // [total_modes] or nullptr
+    float *state;                // [4][total_modes]
+    long long total_modes;
+};
+cudaError_t launch_init_state(const AuxInit &a, cudaStream_t s);
+cudaError_t launch_finalize_state(const float *state, long long total_modes, double *q_end,
+                                  double *qm1_end, cudaStream_t s);
+// a^{steps} = c ybar^{steps-1}, mu^{steps} = a^{steps}; every mode of every instance.
+cudaError_t launch_init_adjoint(const InstDesc *inst, int n_inst, const float *c,
+                                const float *ybar, int steps, float *adj, long long total_modes,
+                                int max_n, cudaStream_t s);
+
+struct GradEpilogue {
+    const InstDesc *inst;
+    int n_inst;
+    long long total_modes, total_k;
+    const double *omega2, *gamma, *dt;  // per mode FP64
+    const float *adj, *gacc, *kacc, *diracc, *tacc;
+    double *d_omega2, *d_gamma, *d_b, *d_c, *d_q0, *d_qm1, *d_tau, *d_kappa, *d_dir;
+};
+cudaError_t launch_grad_epilogue(const GradEpilogue &g, int max_n, cudaStream_t s);
+
+}  // namespace mdx

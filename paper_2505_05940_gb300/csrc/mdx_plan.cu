@@ -1,0 +1,764 @@
+// Host side of libmdx: validation, FP64 -> FP32 coefficient preparation, the
+// plate work assignment, device memory of the plan, and the simulate / grad
+// drivers that enqueue the kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/mdx.h"
+#include "mdx_internal.h"
+
+using namespace mdx;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    if (e == cudaErrorMemoryAllocation)
+        return fail(MDX_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(MDX_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define MDX_CUDA(call, what)                         \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct mdx_plan {
+    int device = 0;
+    int n_inst = 0;
+    long long total_modes = 0;
+    long long total_k = 0;
+    std::vector<InstDesc> inst;
+    std::vector<double> dt;          // per instance
+    // device memory owned by the plan
+    std::vector<void *> allocs;
+    InstDesc *d_inst = nullptr;
+    ModeCoef coef{};
+    double *d_omega2 = nullptr, *d_gamma = nullptr, *d_dt = nullptr;
+    float *d_H = nullptr, *d_dH = nullptr, *d_kappa = nullptr;
+    // plate work assignment
+    int n_cta = 0;
+    PlateItem *d_items = nullptr;
+    int *d_cta_off = nullptr;
+    int npad_max = 4;
+    int state_floats = 0;
+    int ring_stages = 0, stage_bytes = 0;
+    size_t smem_fwd = 0, smem_rev = 0;
+    long long part_stride = 0;
+    float *d_part = nullptr;
+    unsigned *d_counters = nullptr;
+    int *d_abort = nullptr;
+    // tension instances (strings, membranes, linear plates)
+    std::vector<int> tension;
+    int *d_tension = nullptr;
+    int tension_max_n = 1;
+    bool any_plate = false;
+    // scratch for simulate
+    float *d_state = nullptr;        // [4][total_modes]
+    long long wait_limit = 1 << 22;
+    int debug_flags = 0;
+    // optional per-launch timing of the plate kernel
+    bool profiling = false;
+    struct Rec {
+        int which;
+        double bytes;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+    long stat_launch[3] = {0, 0, 0};
+    double stat_ms[3] = {0, 0, 0}, stat_bytes[3] = {0, 0, 0};
+    double H_bytes_per_step = 0, dH_bytes_per_step = 0;
+};
+
+namespace {
+
+int dalloc(mdx_plan *p, void **out, size_t bytes) {
+    *out = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(out, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    p->allocs.push_back(*out);
+    return MDX_OK;
+}
+
+template <class T>
+int upload(mdx_plan *p, T **out, const T *host, size_t n) {
+    int rc = dalloc(p, reinterpret_cast<void **>(out), n * sizeof(T));
+    if (rc) return rc;
+    if (n) MDX_CUDA(cudaMemcpy(*out, host, n * sizeof(T), cudaMemcpyHostToDevice), "upload");
+    return MDX_OK;
+}
+
+bool finite(double x) { return std::isfinite(x); }
+
+int validate(const mdx_instance &I, int i) {
+    if (I.kind != MDX_KIND_TENSION && I.kind != MDX_KIND_PLATE)
+        return fail(MDX_ERR_ARG, "instance %d: unknown kind %d", i, I.kind);
+    if (I.n_phi < 1 || I.n_phi > MDX_MAX_PHI)
+        return fail(MDX_ERR_UNSUPPORTED, "instance %d: n_phi=%d outside [1, %d]", i, I.n_phi,
+                    MDX_MAX_PHI);
+    if (!(I.dt > 0.0) || !finite(I.dt)) return fail(MDX_ERR_ARG, "instance %d: dt must be > 0", i);
+    if (!I.omega2 || !I.gamma || !I.b || !I.c)
+        return fail(MDX_ERR_ARG, "instance %d: omega2, gamma, b and c are required", i);
+    for (int m = 0; m < I.n_phi; ++m) {
+        if (!finite(I.omega2[m]) || !finite(I.gamma[m]) || !finite(I.b[m]) || !finite(I.c[m]))
+            return fail(MDX_ERR_NONFINITE, "instance %d mode %d: non-finite coefficient", i, m);
+        if (!(I.omega2[m] > 0.0))
+            return fail(MDX_ERR_ARG, "instance %d mode %d: omega2 must be > 0", i, m);
+        if (I.gamma[m] < 0.0)
+            return fail(MDX_ERR_UNSTABLE, "instance %d mode %d: gamma < 0 puts a pole in the right half-plane", i, m);
+        if (std::sqrt(I.omega2[m]) * I.dt >= 2.0)
+            return fail(MDX_ERR_UNSTABLE,
+                        "instance %d mode %d: omega*dt = %.4f >= 2 (Stormer-Verlet stability bound)",
+                        i, m, std::sqrt(I.omega2[m]) * I.dt);
+    }
+    if (I.kind == MDX_KIND_TENSION) {
+        if (!I.lambda) return fail(MDX_ERR_ARG, "instance %d: lambda is required for the tension kind", i);
+        if (!finite(I.tau) || I.tau < 0.0) return fail(MDX_ERR_ARG, "instance %d: tau must be finite and >= 0", i);
+        for (int m = 0; m < I.n_phi; ++m)
+            if (!finite(I.lambda[m]) || I.lambda[m] < 0.0)
+                return fail(MDX_ERR_ARG, "instance %d mode %d: lambda must be finite and >= 0", i, m);
+    } else {
+        if (I.n_psi < 0 || I.n_psi > MDX_MAX_PSI)
+            return fail(MDX_ERR_UNSUPPORTED, "instance %d: n_psi=%d outside [0, %d]", i, I.n_psi, MDX_MAX_PSI);
+        if (I.n_psi > 0) {
+            if (!I.H || !I.kappa) return fail(MDX_ERR_ARG, "instance %d: H and kappa are required when n_psi > 0", i);
+            const int N = I.n_phi;
+            for (int k = 0; k < I.n_psi; ++k) {
+                if (!finite(I.kappa[k])) return fail(MDX_ERR_NONFINITE, "instance %d: kappa[%d] is not finite", i, k);
+                const float *Hk = I.H + (size_t)k * N * N;
+                float amax = 0.f;
+                for (size_t t = 0; t < (size_t)N * N; ++t) {
+                    if (!std::isfinite(Hk[t]))
+                        return fail(MDX_ERR_NONFINITE, "instance %d: H[%d] has a non-finite entry", i, k);
+                    amax = std::max(amax, std::fabs(Hk[t]));
+                }
+                for (int a = 0; a < N; ++a)
+                    for (int b = a + 1; b < N; ++b)
+                        if (std::fabs(Hk[(size_t)a * N + b] - Hk[(size_t)b * N + a]) > 1e-5f * amax + 1e-30f)
+                            return fail(MDX_ERR_ARG, "instance %d: H[%d] is not symmetric at (%d, %d)", i, k, a, b);
+                if (I.dH) {
+                    const float *Dk = I.dH + (size_t)k * N * N;
+                    for (size_t t = 0; t < (size_t)N * N; ++t)
+                        if (!std::isfinite(Dk[t]))
+                            return fail(MDX_ERR_NONFINITE, "instance %d: dH[%d] has a non-finite entry", i, k);
+                }
+            }
+        }
+    }
+    return MDX_OK;
+}
+
+// Balance the H bytes of all plate items over at most `max_cta` CTAs.
+struct Piece {
+    int inst, k0, k1;
+    double cost;
+};
+
+}  // namespace
+
+extern "C" {
+
+const char *mdx_last_error(void) { return g_err.c_str(); }
+
+const char *mdx_version(void) { return "mdx 0.1 (sm_103a)"; }
+
+int mdx_plan_destroy(mdx_plan *p) {
+    if (!p) return MDX_OK;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(p->device);
+    cudaDeviceSynchronize();
+    for (auto &r : p->recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (void *a : p->allocs) cudaFree(a);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete p;
+    return MDX_OK;
+}
+
+int mdx_plan_info(const mdx_plan *p, int *n_inst, long *total_modes, long *mode_offset) {
+    if (!p) return fail(MDX_ERR_ARG, "plan is NULL");
+    if (n_inst) *n_inst = p->n_inst;
+    if (total_modes) *total_modes = (long)p->total_modes;
+    if (mode_offset)
+        for (int i = 0; i < p->n_inst; ++i) mode_offset[i] = (long)p->inst[i].mode_off;
+    return MDX_OK;
+}
+
+int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx_options *opts) {
+    if (!out) return fail(MDX_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_inst < 1 || !I) return fail(MDX_ERR_ARG, "need at least one instance");
+    mdx_options o{};
+    if (opts) o = *opts;
+    for (int i = 0; i < n_inst; ++i) {
+        int rc = validate(I[i], i);
+        if (rc) return rc;
+    }
+    MDX_CUDA(cudaSetDevice(o.device), "cudaSetDevice");
+    mdx_plan *p = new mdx_plan();
+    p->device = o.device;
+    p->n_inst = n_inst;
+    if (o.wait_limit > 0) p->wait_limit = o.wait_limit;
+    p->debug_flags = o.debug_flags;
+    auto bail = [&](int rc) {
+        mdx_plan_destroy(p);
+        return rc;
+    };
+
+    // ---- per-instance layout and FP64 -> FP32 coefficients (difference form)
+    std::vector<float> eps, rw2, rw2lo, r, b, c, lam;
+    std::vector<double> w2d, gmd, dtd;
+    std::vector<float> kap;
+    long long H_total = 0;
+    p->inst.resize(n_inst);
+    p->dt.resize(n_inst);
+    bool any_dir = false;
+    for (int i = 0; i < n_inst; ++i) {
+        const mdx_instance &S = I[i];
+        InstDesc d{};
+        d.kind = S.kind;
+        d.N = S.n_phi;
+        d.M = (S.kind == MDX_KIND_PLATE) ? S.n_psi : 0;
+        d.Npad = (S.n_phi + 3) & ~3;
+        d.mode_off = p->total_modes;
+        d.k_off = p->total_k;
+        d.taup = (S.kind == MDX_KIND_TENSION) ? (float)S.tau : 0.f;
+        d.H_off = H_total;
+        d.has_dir = (d.M > 0 && S.dH) ? 1 : 0;
+        any_dir = any_dir || d.has_dir;
+        if (d.M > 0) H_total += (long long)d.M * d.N * d.Npad;
+        p->total_modes += d.N;
+        p->total_k += d.M;
+        p->dt[i] = S.dt;
+        const double T = S.dt;
+        for (int m = 0; m < S.n_phi; ++m) {
+            const double den = 1.0 + S.gamma[m] * T;
+            const double rr = T * T / den;
+            eps.push_back((float)(2.0 * S.gamma[m] * T / den));
+            const double rw = rr * S.omega2[m];
+            rw2.push_back((float)rw);
+            rw2lo.push_back((float)(rw - (double)(float)rw));
+            r.push_back((float)rr);
+            b.push_back((float)S.b[m]);
+            c.push_back((float)S.c[m]);
+            lam.push_back(S.kind == MDX_KIND_TENSION ? (float)S.lambda[m] : 0.f);
+            w2d.push_back(S.omega2[m]);
+            gmd.push_back(S.gamma[m]);
+            dtd.push_back(T);
+        }
+        for (int k = 0; k < d.M; ++k) kap.push_back((float)S.kappa[k]);
+        p->inst[i] = d;
+    }
+    const size_t TM = (size_t)p->total_modes;
+    {
+        std::vector<float> all;
+        all.reserve(7 * TM);
+        for (auto *v : {&eps, &rw2, &r, &b, &c, &lam, &rw2lo}) all.insert(all.end(), v->begin(), v->end());
+        float *dc = nullptr;
+        int rc = upload(p, &dc, all.data(), all.size());
+        if (rc) return bail(rc);
+        p->coef.eps = dc;
+        p->coef.rw2 = dc + TM;
+        p->coef.r = dc + 2 * TM;
+        p->coef.b = dc + 3 * TM;
+        p->coef.c = dc + 4 * TM;
+        p->coef.lam = dc + 5 * TM;
+        p->coef.rw2lo = dc + 6 * TM;
+        if ((rc = upload(p, &p->d_omega2, w2d.data(), TM))) return bail(rc);
+        if ((rc = upload(p, &p->d_gamma, gmd.data(), TM))) return bail(rc);
+        if ((rc = upload(p, &p->d_dt, dtd.data(), TM))) return bail(rc);
+        if ((rc = upload(p, &p->d_kappa, kap.data(), kap.size()))) return bail(rc);
+    }
+    // ---- coupling tensors: [M][N][Npad], rows zero padded
+    if (H_total > 0) {
+        int rc = dalloc(p, reinterpret_cast<void **>(&p->d_H), H_total * sizeof(float));
+        if (rc) return bail(rc);
+        if (any_dir) {
+            rc = dalloc(p, reinterpret_cast<void **>(&p->d_dH), H_total * sizeof(float));
+            if (rc) return bail(rc);
+            MDX_CUDA(cudaMemset(p->d_dH, 0, H_total * sizeof(float)), "memset dH");
+        }
+        std::vector<float> tmp;
+        for (int i = 0; i < n_inst; ++i) {
+            const InstDesc &d = p->inst[i];
+            if (d.M == 0) continue;
+            const size_t blk = (size_t)d.M * d.N * d.Npad;
+            for (int which = 0; which < (d.has_dir ? 2 : 1); ++which) {
+                const float *src = which == 0 ? I[i].H : I[i].dH;
+                tmp.assign(blk, 0.f);
+                for (int k = 0; k < d.M; ++k)
+                    for (int a = 0; a < d.N; ++a)
+                        std::memcpy(&tmp[((size_t)k * d.N + a) * d.Npad],
+                                    src + ((size_t)k * d.N + a) * d.N, d.N * sizeof(float));
+                float *dst = (which == 0 ? p->d_H : p->d_dH) + d.H_off;
+                MDX_CUDA(cudaMemcpy(dst, tmp.data(), blk * sizeof(float), cudaMemcpyHostToDevice),
+                         "upload H");
+            }
+        }
+    }
+    for (int i = 0; i < n_inst; ++i) {
+        InstDesc &d = p->inst[i];
+        d.dH_off = d.H_off;
+        // algorithmic bytes of one pass: the N x N block of every stress mode
+        p->H_bytes_per_step += 4.0 * d.M * d.N * d.N;
+        if (d.has_dir) p->dH_bytes_per_step += 4.0 * d.M * d.N * d.N;
+    }
+
+    // ---- tension list (strings, membranes and plates without coupling)
+    for (int i = 0; i < n_inst; ++i) {
+        const InstDesc &d = p->inst[i];
+        if (d.kind == MDX_KIND_TENSION || d.M == 0) {
+            p->tension.push_back(i);
+            p->tension_max_n = std::max(p->tension_max_n, d.N);
+        } else {
+            p->any_plate = true;
+        }
+    }
+
+    // ---- plate work assignment
+    std::vector<PlateItem> items;
+    std::vector<int> cta_off{0};
+    if (p->any_plate) {
+        int dev_sms = 0, smem_optin = 0;
+        MDX_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, p->device), "attr");
+        MDX_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device), "attr");
+        int max_cta = dev_sms;
+        if (o.max_ctas > 0) max_cta = std::min(max_cta, o.max_ctas);
+        std::vector<Piece> pieces;
+        double total = 0.0;
+        long long total_kk = 0;
+        for (int i = 0; i < n_inst; ++i) {
+            const InstDesc &d = p->inst[i];
+            if (d.M == 0) continue;
+            total += (double)d.M * d.N * d.Npad;
+            total_kk += d.M;
+        }
+        const int G = (int)std::min<long long>(max_cta, total_kk);
+        const double target = total / G;
+        for (int i = 0; i < n_inst; ++i) {
+            const InstDesc &d = p->inst[i];
+            if (d.M == 0) continue;
+            const double cost = (double)d.M * d.N * d.Npad;
+            int np = (int)std::lround(cost / target);
+            np = std::max(1, std::min(np, std::min(d.M, G)));
+            if (o.force_split > 0) np = std::max(np, std::min(o.force_split, std::min(d.M, G)));
+            for (int j = 0; j < np; ++j) {
+                const int k0 = (int)((long long)d.M * j / np);
+                const int k1 = (int)((long long)d.M * (j + 1) / np);
+                pieces.push_back({i, k0, k1, (double)(k1 - k0) * d.N * d.Npad});
+            }
+        }
+        std::stable_sort(pieces.begin(), pieces.end(),
+                         [](const Piece &a, const Piece &b) { return a.cost > b.cost; });
+        // state budget per CTA in floats
+        const int state_cap = 24 * 1024;   // 96 KB of item state per CTA at most
+        std::vector<double> load(G, 0.0);
+        std::vector<int> sfl(G, 0);
+        std::vector<std::vector<Piece>> per(G);
+        for (const Piece &pc : pieces) {
+            const InstDesc &d = p->inst[pc.inst];
+            const int need = ST_NARR * d.Npad;
+            int best = -1;
+            for (int g = 0; g < G; ++g) {
+                bool has = false;
+                for (const Piece &q : per[g]) has = has || (q.inst == pc.inst);
+                if (has || sfl[g] + need > state_cap) continue;
+                if (best < 0 || load[g] < load[best]) best = g;
+            }
+            if (best < 0)
+                return bail(fail(MDX_ERR_UNSUPPORTED,
+                                 "plate work does not fit: too many plate modes for %d CTAs", G));
+            per[best].push_back(pc);
+            load[best] += pc.cost;
+            sfl[best] += need;
+        }
+        // contributors per instance, in CTA order
+        std::vector<std::vector<int>> contrib(n_inst);
+        for (int g = 0; g < G; ++g)
+            for (const Piece &q : per[g]) contrib[q.inst].push_back(g);
+        long long part_off = 0;
+        for (int i = 0; i < n_inst; ++i) {
+            InstDesc &d = p->inst[i];
+            d.n_contrib = (int)contrib[i].size();
+            d.part_off = part_off;
+            if (d.n_contrib > 1) part_off += (long long)d.n_contrib * 3 * d.Npad;
+        }
+        p->part_stride = std::max<long long>(part_off, 4);
+        int max_state = 0;
+        for (int g = 0; g < G; ++g) {
+            if (per[g].empty()) continue;
+            int soff = 0;
+            std::sort(per[g].begin(), per[g].end(),
+                      [](const Piece &a, const Piece &b) { return a.inst < b.inst; });
+            for (const Piece &q : per[g]) {
+                const InstDesc &d = p->inst[q.inst];
+                PlateItem it{};
+                it.inst = q.inst;
+                it.k0 = q.k0;
+                it.k1 = q.k1;
+                const auto &cl = contrib[q.inst];
+                it.slot = (int)(std::find(cl.begin(), cl.end(), g) - cl.begin());
+                it.owner = (it.slot == 0) ? 1 : 0;
+                it.smem_state = soff;
+                soff += ST_NARR * d.Npad;
+                items.push_back(it);
+                p->npad_max = std::max(p->npad_max, d.Npad);
+            }
+            max_state = std::max(max_state, soff);
+            cta_off.push_back((int)items.size());
+        }
+        p->n_cta = (int)cta_off.size() - 1;
+        p->state_floats = max_state;
+        // ring: stages of >= one padded row, fill the remaining shared memory
+        int stage = o.stage_bytes > 0 ? o.stage_bytes : 32 * 1024;
+        stage = std::max(stage, p->npad_max * 4);
+        stage = (stage + 15) & ~15;
+        const size_t fixed = plate_smem_bytes(0, stage, p->npad_max, p->state_floats);
+        int ring = o.ring_stages > 0 ? o.ring_stages
+                                     : (int)((size_t)(smem_optin - 1024 - fixed) / stage);
+        ring = std::max(2, std::min(ring, 16));
+        p->ring_stages = ring;
+        p->stage_bytes = stage;
+        p->smem_fwd = p->smem_rev = plate_smem_bytes(ring, stage, p->npad_max, p->state_floats);
+        if (p->smem_fwd > (size_t)smem_optin)
+            return bail(fail(MDX_ERR_UNSUPPORTED, "plate kernel needs %zu B of shared memory (> %d)",
+                             p->smem_fwd, smem_optin));
+        int rc;
+        if ((rc = upload(p, &p->d_items, items.data(), items.size()))) return bail(rc);
+        if ((rc = upload(p, &p->d_cta_off, cta_off.data(), cta_off.size()))) return bail(rc);
+        if ((rc = dalloc(p, reinterpret_cast<void **>(&p->d_part), 2 * p->part_stride * sizeof(float)))) return bail(rc);
+    }
+    int rc;
+    if ((rc = upload(p, &p->d_inst, p->inst.data(), p->inst.size()))) return bail(rc);
+    if ((rc = upload(p, &p->d_tension, p->tension.data(), p->tension.size()))) return bail(rc);
+    if ((rc = dalloc(p, reinterpret_cast<void **>(&p->d_counters), n_inst * sizeof(unsigned)))) return bail(rc);
+    if ((rc = dalloc(p, reinterpret_cast<void **>(&p->d_abort), 16))) return bail(rc);
+    if ((rc = dalloc(p, reinterpret_cast<void **>(&p->d_state), kStateArrays * TM * sizeof(float)))) return bail(rc);
+    *out = p;
+    return MDX_OK;
+}
+
+size_t mdx_checkpoint_bytes(const mdx_plan *p, int steps, int K) {
+    if (!p || steps <= 0 || K <= 0) return 0;
+    const size_t nck = (size_t)((steps + K - 1) / K);
+    return nck * kStateArrays * (size_t)p->total_modes * sizeof(float);
+}
+
+}  // extern "C"
+
+namespace {
+
+PlateParams base_plate(mdx_plan *p, int mode, int steps, int n_begin, int total_steps) {
+    PlateParams P{};
+    P.inst = p->d_inst;
+    P.items = p->d_items;
+    P.cta_item_off = p->d_cta_off;
+    P.coef = p->coef;
+    P.H = p->d_H;
+    P.dH = p->d_dH;
+    P.kappa = p->d_kappa;
+    P.n_inst = p->n_inst;
+    P.steps = steps;
+    P.n_begin = n_begin;
+    P.total_steps = total_steps;
+    P.mode = mode;
+    P.stage_bytes = p->stage_bytes;
+    P.ring_stages = p->ring_stages;
+    P.max_spt = (p->npad_max + kPlateThreads - 1) / kPlateThreads;
+    P.smem_state_floats = p->state_floats;
+    P.total_modes = p->total_modes;
+    P.part = p->d_part;
+    P.part_stride = p->part_stride;
+    P.counters = p->d_counters;
+    P.abort_flag = p->d_abort;
+    P.wait_limit = p->wait_limit;
+    P.debug_flags = p->debug_flags;
+    return P;
+}
+
+TensionParams base_tension(mdx_plan *p, int mode, int steps, int n_begin, int total_steps) {
+    TensionParams T{};
+    T.inst = p->d_inst;
+    T.list = p->d_tension;
+    T.n_list = (int)p->tension.size();
+    T.coef = p->coef;
+    T.steps = steps;
+    T.n_begin = n_begin;
+    T.total_steps = total_steps;
+    T.mode = mode;
+    T.total_modes = p->total_modes;
+    return T;
+}
+
+int run_segment(mdx_plan *p, PlateParams &P, TensionParams &T, cudaStream_t s) {
+    if (!p->tension.empty()) MDX_CUDA(launch_tension(T, p->tension_max_n, s), "tension kernel");
+    if (p->any_plate) {
+        MDX_CUDA(cudaMemsetAsync(p->d_counters, 0, p->n_inst * sizeof(unsigned), s), "memset");
+        MDX_CUDA(cudaMemsetAsync(p->d_abort, 0, sizeof(int), s), "memset");
+        const size_t smem = (P.mode == MODE_REVERSE) ? p->smem_rev : p->smem_fwd;
+        mdx_plan::Rec rec{};
+        if (p->profiling) {
+            rec.which = P.mode;
+            rec.bytes = (double)P.steps * (p->H_bytes_per_step +
+                                           (P.mode == MODE_REVERSE ? p->dH_bytes_per_step : 0.0));
+            MDX_CUDA(cudaEventCreate(&rec.a), "event");
+            MDX_CUDA(cudaEventCreate(&rec.b), "event");
+            MDX_CUDA(cudaEventRecord(rec.a, s), "event");
+        }
+        MDX_CUDA(launch_plate(P, p->n_cta, smem, s), "plate kernel");
+        if (p->profiling) {
+            MDX_CUDA(cudaEventRecord(rec.b, s), "event");
+            p->recs.push_back(rec);
+        }
+    }
+    return MDX_OK;
+}
+
+}  // namespace
+
+extern "C" int mdx_simulate(mdx_plan *p, const float *exc, const double *q0, const double *qm1,
+                            int steps, float *audio, double *q_end, double *qm1_end, int K,
+                            void *ckpt, int *status, void *stream) {
+    if (!p) return fail(MDX_ERR_ARG, "plan is NULL");
+    if (steps < 0) return fail(MDX_ERR_ARG, "steps must be >= 0");
+    if (ckpt && K <= 0) return fail(MDX_ERR_ARG, "checkpoint interval K must be > 0");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    MDX_CUDA(cudaSetDevice(p->device), "cudaSetDevice");
+    if (status) MDX_CUDA(cudaMemsetAsync(status, 0, p->n_inst * sizeof(int), s), "memset status");
+    AuxInit a{q0, qm1, p->d_state, p->total_modes};
+    MDX_CUDA(launch_init_state(a, s), "init state");
+    if (steps > 0) {
+        PlateParams P = base_plate(p, MODE_FORWARD, steps, 0, steps);
+        TensionParams T = base_tension(p, MODE_FORWARD, steps, 0, steps);
+        P.exc = T.exc = exc;
+        P.audio = T.audio = audio;
+        P.state_io = T.state_io = p->d_state;
+        P.ckpt_K = T.ckpt_K = ckpt ? K : 1 << 30;
+        P.ckpt = T.ckpt = static_cast<float *>(ckpt);
+        P.status = T.status = status;
+        int rc = run_segment(p, P, T, s);
+        if (rc) return rc;
+    }
+    MDX_CUDA(launch_finalize_state(p->d_state, p->total_modes, q_end, qm1_end, s), "finalize");
+    return MDX_OK;
+}
+
+namespace {
+
+struct GradWork {
+    float *seg_q, *seg_v, *adj, *gacc, *kacc, *diracc, *tacc;
+    size_t bytes;
+};
+
+GradWork grad_layout(const mdx_plan *p, int K, void *base) {
+    const size_t TM = (size_t)p->total_modes, TK = (size_t)std::max<long long>(p->total_k, 1);
+    auto al = [](size_t x) { return (x + 63) & ~size_t(63); };
+    size_t off = 0;
+    GradWork w{};
+    char *b = static_cast<char *>(base);
+    auto take = [&](size_t floats) {
+        float *ptr = b ? reinterpret_cast<float *>(b + off) : nullptr;
+        off += al(floats * sizeof(float));
+        return ptr;
+    };
+    w.seg_q = take((size_t)(K + 1) * TM);
+    w.seg_v = take((size_t)(K + 1) * TM);
+    w.adj = take(AD_N * TM);
+    w.gacc = take(2 * GA_N * TM);
+    w.kacc = take(2 * TK);
+    w.diracc = take(2 * TK);
+    w.tacc = take(2 * (size_t)p->n_inst);
+    w.bytes = off;
+    return w;
+}
+
+}  // namespace
+
+extern "C" size_t mdx_grad_workspace_bytes(const mdx_plan *p, int steps, int K) {
+    if (!p || K <= 0) return 0;
+    (void)steps;
+    return grad_layout(p, K, nullptr).bytes;
+}
+
+extern "C" int mdx_grad(mdx_plan *p, const float *exc, const double *q0, const double *qm1,
+                        int steps, const float *d_audio, int K, const void *ckpt, void *work,
+                        size_t work_bytes, const mdx_grads *out, int *status, void *stream) {
+    if (!p) return fail(MDX_ERR_ARG, "plan is NULL");
+    if (steps <= 0) return fail(MDX_ERR_ARG, "steps must be > 0");
+    if (K <= 0 || !ckpt) return fail(MDX_ERR_ARG, "mdx_grad needs the checkpoints of mdx_simulate (K > 0)");
+    if (!d_audio) return fail(MDX_ERR_ARG, "d_audio is required");
+    GradWork w = grad_layout(p, K, work);
+    if (!work || work_bytes < w.bytes)
+        return fail(MDX_ERR_ARG, "workspace of %zu bytes is smaller than the %zu bytes required",
+                    work_bytes, w.bytes);
+    (void)q0;
+    (void)qm1;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    MDX_CUDA(cudaSetDevice(p->device), "cudaSetDevice");
+    if (status) MDX_CUDA(cudaMemsetAsync(status, 0, p->n_inst * sizeof(int), s), "memset status");
+    const size_t TM = (size_t)p->total_modes, TK = (size_t)std::max<long long>(p->total_k, 1);
+    MDX_CUDA(cudaMemsetAsync(w.gacc, 0, 2 * GA_N * TM * sizeof(float), s), "memset");
+    MDX_CUDA(cudaMemsetAsync(w.kacc, 0, 2 * TK * sizeof(float), s), "memset");
+    MDX_CUDA(cudaMemsetAsync(w.diracc, 0, 2 * TK * sizeof(float), s), "memset");
+    MDX_CUDA(cudaMemsetAsync(w.tacc, 0, 2 * p->n_inst * sizeof(float), s), "memset");
+    MDX_CUDA(launch_init_adjoint(p->d_inst, p->n_inst, p->coef.c, d_audio, steps, w.adj,
+                                 p->total_modes, 0, s),
+             "init adjoint");
+    const int nseg = (steps + K - 1) / K;
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+        const int n0 = sg * K;
+        const int L = std::min(K, steps - n0);
+        // recompute the segment from its checkpoint, storing every state
+        PlateParams P = base_plate(p, MODE_RECOMPUTE, L, n0, steps);
+        TensionParams T = base_tension(p, MODE_RECOMPUTE, L, n0, steps);
+        P.exc = T.exc = exc;
+        P.ckpt_K = T.ckpt_K = K;
+        P.ckpt = T.ckpt = const_cast<float *>(static_cast<const float *>(ckpt));
+        P.seg_q = T.seg_q = w.seg_q;
+        P.seg_v = T.seg_v = w.seg_v;
+        P.status = T.status = status;
+        int rc = run_segment(p, P, T, s);
+        if (rc) return rc;
+        // adjoint sweep over the segment
+        P.mode = T.mode = MODE_REVERSE;
+        P.ybar = T.ybar = d_audio;
+        P.adj = T.adj = w.adj;
+        P.gacc = T.gacc = w.gacc;
+        P.kacc = w.kacc;
+        P.diracc = w.diracc;
+        T.tacc = w.tacc;
+        rc = run_segment(p, P, T, s);
+        if (rc) return rc;
+    }
+    GradEpilogue g{};
+    g.inst = p->d_inst;
+    g.n_inst = p->n_inst;
+    g.total_modes = p->total_modes;
+    g.total_k = p->total_k;
+    g.omega2 = p->d_omega2;
+    g.gamma = p->d_gamma;
+    g.dt = p->d_dt;
+    g.adj = w.adj;
+    g.gacc = w.gacc;
+    g.kacc = w.kacc;
+    g.diracc = w.diracc;
+    g.tacc = w.tacc;
+    if (out) {
+        g.d_omega2 = out->d_omega2;
+        g.d_gamma = out->d_gamma;
+        g.d_b = out->d_b;
+        g.d_c = out->d_c;
+        g.d_q0 = out->d_q0;
+        g.d_qm1 = out->d_qm1;
+        g.d_tau = out->d_tau;
+        g.d_kappa = out->d_kappa;
+        g.d_dir = out->d_dir;
+    }
+    MDX_CUDA(launch_grad_epilogue(g, 0, s), "grad epilogue");
+    return MDX_OK;
+}
+
+extern "C" int mdx_coeffs_from_physics(int n, const double *lambda, double D, double T0, double rho,
+                                       double s0, double s1, double *omega2, double *gamma) {
+    if (n < 0 || !lambda || !omega2 || !gamma) return fail(MDX_ERR_ARG, "null argument");
+    if (!(rho > 0.0)) return fail(MDX_ERR_ARG, "rho must be > 0");
+    for (int m = 0; m < n; ++m) {
+        const double l = lambda[m];
+        omega2[m] = (D * l * l + T0 * l) / rho;   // Sec. 3.2, Eq. 13
+        gamma[m] = s0 + s1 * omega2[m];           // damping family of Eq. 14
+    }
+    return MDX_OK;
+}
+
+extern "C" int mdx_coeffs_vjp(int n, const double *lambda, double D, double T0, double rho,
+                              double s0, double s1, const double *d_omega2, const double *d_gamma,
+                              double *dD, double *dT0, double *ds0, double *ds1, double *d_lambda) {
+    if (n < 0 || !lambda || !d_omega2 || !d_gamma) return fail(MDX_ERR_ARG, "null argument");
+    (void)s0;
+    double aD = 0, aT = 0, a0 = 0, a1 = 0;
+    for (int m = 0; m < n; ++m) {
+        const double l = lambda[m];
+        const double w2 = (D * l * l + T0 * l) / rho;
+        const double gw = d_omega2[m] + s1 * d_gamma[m];   // total derivative through gamma(omega2)
+        aD += gw * l * l / rho;
+        aT += gw * l / rho;
+        a0 += d_gamma[m];
+        a1 += d_gamma[m] * w2;
+        if (d_lambda) d_lambda[m] = gw * (2.0 * D * l + T0) / rho;
+    }
+    if (dD) *dD = aD;
+    if (dT0) *dT0 = aT;
+    if (ds0) *ds0 = a0;
+    if (ds1) *ds1 = a1;
+    return MDX_OK;
+}
+
+extern "C" int mdx_plan_set_profiling(mdx_plan *p, int enable) {
+    if (!p) return fail(MDX_ERR_ARG, "plan is NULL");
+    p->profiling = enable != 0;
+    return MDX_OK;
+}
+
+extern "C" int mdx_plan_reset_stats(mdx_plan *p) {
+    if (!p) return fail(MDX_ERR_ARG, "plan is NULL");
+    for (auto &r : p->recs) {
+        cudaEventSynchronize(r.b);
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    p->recs.clear();
+    for (int i = 0; i < 3; ++i) p->stat_launch[i] = 0, p->stat_ms[i] = 0, p->stat_bytes[i] = 0;
+    return MDX_OK;
+}
+
+extern "C" int mdx_plan_kernel_stats(mdx_plan *p, int which, long *launches, double *ms,
+                                     double *bytes) {
+    if (!p) return fail(MDX_ERR_ARG, "plan is NULL");
+    if (which < 0 || which > 2) return fail(MDX_ERR_ARG, "which must be 0, 1 or 2");
+    for (auto &r : p->recs) {
+        MDX_CUDA(cudaEventSynchronize(r.b), "event sync");
+        float t = 0.f;
+        MDX_CUDA(cudaEventElapsedTime(&t, r.a, r.b), "elapsed");
+        p->stat_launch[r.which] += 1;
+        p->stat_ms[r.which] += t;
+        p->stat_bytes[r.which] += r.bytes;
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    p->recs.clear();
+    if (launches) *launches = p->stat_launch[which];
+    if (ms) *ms = p->stat_ms[which];
+    if (bytes) *bytes = p->stat_bytes[which];
+    return MDX_OK;
+}
