@@ -26,6 +26,7 @@ constexpr int kPlateBlock = kPlateThreads + 32 * kProducerWarps;
 constexpr int kStateArrays = 4;      // q_hi, q_lo, v_hi, v_lo
 constexpr int kMaxSpt = 4;             // modes per consumer thread (N_pad <= 1024)
 constexpr int kChunkK = 4;             // stress modes reduced together
+constexpr int kUPartFloats = 1024;     // row groups x N_pad <= 256 threads x 4 columns
 constexpr int kTensionWarpsPerBlock = 4;
 constexpr int kTensionMaxJ = 32;       // modes per lane (N <= 1024)
 
@@ -108,6 +109,7 @@ struct PlateParams {
     int mode;                     // KernelMode
     int stage_bytes;
     int ring_stages;
+    int u_slots;                  // row-group partial-sum slots: 1 forward, 2-3 reverse
     int max_spt;
     int smem_state_floats;
     // forward I/O
@@ -156,7 +158,7 @@ struct TensionParams {
 };
 
 // Launchers (defined in the kernel translation units).
-size_t plate_smem_bytes(int ring_stages, int stage_bytes, int npad_max, int state_floats);
+size_t plate_smem_bytes(int ring_stages, int stage_bytes, int u_slots, int state_floats);
 cudaError_t launch_plate(const PlateParams &p, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_tension(const TensionParams &p, int max_n, cudaStream_t s);
 

@@ -69,7 +69,7 @@ struct mdx_plan {
     int *d_cta_off = nullptr;
     int npad_max = 4;
     int state_floats = 0;
-    int ring_stages = 0, stage_bytes = 0;
+    int ring_fwd = 0, ring_rev = 0, stage_bytes = 0, u_slots_fwd = 1, u_slots_rev = 2;
     size_t smem_fwd = 0, smem_rev = 0;
     long long part_stride = 0;
     float *d_part = nullptr;
@@ -355,7 +355,12 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
         MDX_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device), "attr");
         int max_cta = dev_sms;
         if (o.max_ctas > 0) max_cta = std::min(max_cta, o.max_ctas);
-        std::vector<Piece> pieces;
+        // Contiguous split: walk all (plate, stress mode) units in plan order
+        // and cut the running H-byte count into G equal parts; each CTA then
+        // holds at most one contiguous k range per plate.  A forced split
+        // (tests) or an overfull shared-memory state falls back to
+        // longest-processing-time assignment of explicit pieces.
+        const int state_cap = 24 * 1024;   // 96 KB of item state per CTA at most
         double total = 0.0;
         long long total_kk = 0;
         for (int i = 0; i < n_inst; ++i) {
@@ -366,42 +371,70 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
         }
         const int G = (int)std::min<long long>(max_cta, total_kk);
         const double target = total / G;
-        for (int i = 0; i < n_inst; ++i) {
-            const InstDesc &d = p->inst[i];
-            if (d.M == 0) continue;
-            const double cost = (double)d.M * d.N * d.Npad;
-            int np = (int)std::lround(cost / target);
-            np = std::max(1, std::min(np, std::min(d.M, G)));
-            if (o.force_split > 0) np = std::max(np, std::min(o.force_split, std::min(d.M, G)));
-            for (int j = 0; j < np; ++j) {
-                const int k0 = (int)((long long)d.M * j / np);
-                const int k1 = (int)((long long)d.M * (j + 1) / np);
-                pieces.push_back({i, k0, k1, (double)(k1 - k0) * d.N * d.Npad});
+        std::vector<std::vector<Piece>> per(G);
+        bool contiguous_ok = (o.force_split <= 0);
+        if (contiguous_ok) {
+            double cum = 0.0;
+            for (int i = 0; i < n_inst; ++i) {
+                const InstDesc &d = p->inst[i];
+                if (d.M == 0) continue;
+                const double c = (double)d.N * d.Npad;
+                for (int k = 0; k < d.M; ++k) {
+                    int g = (int)((cum + 0.5 * c) / target);
+                    g = std::max(0, std::min(G - 1, g));
+                    cum += c;
+                    auto &v = per[g];
+                    if (!v.empty() && v.back().inst == i && v.back().k1 == k) {
+                        v.back().k1 = k + 1;
+                        v.back().cost += c;
+                    } else {
+                        v.push_back({i, k, k + 1, c});
+                    }
+                }
+            }
+            for (int g = 0; g < G && contiguous_ok; ++g) {
+                int need = 0;
+                for (const Piece &q : per[g]) need += ST_NARR * p->inst[q.inst].Npad;
+                if (need > state_cap) contiguous_ok = false;
             }
         }
-        std::stable_sort(pieces.begin(), pieces.end(),
-                         [](const Piece &a, const Piece &b) { return a.cost > b.cost; });
-        // state budget per CTA in floats
-        const int state_cap = 24 * 1024;   // 96 KB of item state per CTA at most
-        std::vector<double> load(G, 0.0);
-        std::vector<int> sfl(G, 0);
-        std::vector<std::vector<Piece>> per(G);
-        for (const Piece &pc : pieces) {
-            const InstDesc &d = p->inst[pc.inst];
-            const int need = ST_NARR * d.Npad;
-            int best = -1;
-            for (int g = 0; g < G; ++g) {
-                bool has = false;
-                for (const Piece &q : per[g]) has = has || (q.inst == pc.inst);
-                if (has || sfl[g] + need > state_cap) continue;
-                if (best < 0 || load[g] < load[best]) best = g;
+        if (!contiguous_ok) {
+            for (auto &v : per) v.clear();
+            std::vector<Piece> pieces;
+            for (int i = 0; i < n_inst; ++i) {
+                const InstDesc &d = p->inst[i];
+                if (d.M == 0) continue;
+                const double cost = (double)d.M * d.N * d.Npad;
+                int np = (int)std::ceil(cost / target - 1e-9);
+                np = std::max(1, std::min(np, std::min(d.M, G)));
+                if (o.force_split > 0) np = std::max(np, std::min(o.force_split, std::min(d.M, G)));
+                for (int j = 0; j < np; ++j) {
+                    const int k0 = (int)((long long)d.M * j / np);
+                    const int k1 = (int)((long long)d.M * (j + 1) / np);
+                    pieces.push_back({i, k0, k1, (double)(k1 - k0) * d.N * d.Npad});
+                }
             }
-            if (best < 0)
-                return bail(fail(MDX_ERR_UNSUPPORTED,
-                                 "plate work does not fit: too many plate modes for %d CTAs", G));
-            per[best].push_back(pc);
-            load[best] += pc.cost;
-            sfl[best] += need;
+            std::stable_sort(pieces.begin(), pieces.end(),
+                             [](const Piece &a, const Piece &b) { return a.cost > b.cost; });
+            std::vector<double> load(G, 0.0);
+            std::vector<int> sfl(G, 0);
+            for (const Piece &pc : pieces) {
+                const InstDesc &d = p->inst[pc.inst];
+                const int need = ST_NARR * d.Npad;
+                int best = -1;
+                for (int g = 0; g < G; ++g) {
+                    bool has = false;
+                    for (const Piece &q : per[g]) has = has || (q.inst == pc.inst);
+                    if (has || sfl[g] + need > state_cap) continue;
+                    if (best < 0 || load[g] < load[best]) best = g;
+                }
+                if (best < 0)
+                    return bail(fail(MDX_ERR_UNSUPPORTED,
+                                     "plate work does not fit: too many plate modes for %d CTAs", G));
+                per[best].push_back(pc);
+                load[best] += pc.cost;
+                sfl[best] += need;
+            }
         }
         // contributors per instance, in CTA order
         std::vector<std::vector<int>> contrib(n_inst);
@@ -440,20 +473,40 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
         }
         p->n_cta = (int)cta_off.size() - 1;
         p->state_floats = max_state;
-        // ring: stages of >= one padded row, fill the remaining shared memory
-        int stage = o.stage_bytes > 0 ? o.stage_bytes : 32 * 1024;
+        // ring: stages of >= one padded row, filling the remaining shared memory
+        // default stage: 64 KB (fewer ring turnovers per byte), halved until
+        // at least two stages fit beside the reverse sweep's buffers
+        int stage = o.stage_bytes > 0 ? o.stage_bytes : 64 * 1024;
         stage = std::max(stage, p->npad_max * 4);
         stage = (stage + 15) & ~15;
-        const size_t fixed = plate_smem_bytes(0, stage, p->npad_max, p->state_floats);
-        int ring = o.ring_stages > 0 ? o.ring_stages
-                                     : (int)((size_t)(smem_optin - 1024 - fixed) / stage);
-        ring = std::max(2, std::min(ring, 16));
-        p->ring_stages = ring;
+        if (o.stage_bytes <= 0) {
+            while (stage > 16 * 1024 && stage / 2 >= p->npad_max * 4 &&
+                   plate_smem_bytes(2, stage, 3, p->state_floats) + 1024 > (size_t)smem_optin)
+                stage = ((stage / 2) + 15) & ~15;
+        }
         p->stage_bytes = stage;
-        p->smem_fwd = p->smem_rev = plate_smem_bytes(ring, stage, p->npad_max, p->state_floats);
-        if (p->smem_fwd > (size_t)smem_optin)
-            return bail(fail(MDX_ERR_UNSUPPORTED, "plate kernel needs %zu B of shared memory (> %d)",
-                             p->smem_fwd, smem_optin));
+        bool dir = false;
+        for (const auto &d : p->inst) dir = dir || d.has_dir;
+        p->u_slots_fwd = 1;
+        p->u_slots_rev = dir ? 3 : 2;
+        for (int which = 0; which < 2; ++which) {
+            const int us = which == 0 ? p->u_slots_fwd : p->u_slots_rev;
+            const size_t fixed = plate_smem_bytes(0, stage, us, p->state_floats);
+            if (fixed + 2 * (size_t)stage + 1024 > (size_t)smem_optin)
+                return bail(fail(MDX_ERR_UNSUPPORTED,
+                                 "plate kernel needs %zu B of shared memory (> %d)",
+                                 fixed + 2 * (size_t)stage, smem_optin));
+            int ring = o.ring_stages > 0 ? o.ring_stages
+                                         : (int)((size_t)(smem_optin - 1024 - fixed) / stage);
+            ring = std::max(2, std::min(ring, 16));
+            const size_t need = plate_smem_bytes(ring, stage, us, p->state_floats);
+            if (need > (size_t)smem_optin)
+                return bail(fail(MDX_ERR_UNSUPPORTED,
+                                 "plate kernel needs %zu B of shared memory (> %d)", need,
+                                 smem_optin));
+            (which == 0 ? p->ring_fwd : p->ring_rev) = ring;
+            (which == 0 ? p->smem_fwd : p->smem_rev) = need;
+        }
         int rc;
         if ((rc = upload(p, &p->d_items, items.data(), items.size()))) return bail(rc);
         if ((rc = upload(p, &p->d_cta_off, cta_off.data(), cta_off.size()))) return bail(rc);
@@ -494,7 +547,8 @@ PlateParams base_plate(mdx_plan *p, int mode, int steps, int n_begin, int total_
     P.total_steps = total_steps;
     P.mode = mode;
     P.stage_bytes = p->stage_bytes;
-    P.ring_stages = p->ring_stages;
+    P.ring_stages = (mode == MODE_REVERSE) ? p->ring_rev : p->ring_fwd;
+    P.u_slots = (mode == MODE_REVERSE) ? p->u_slots_rev : p->u_slots_fwd;
     P.max_spt = (p->npad_max + kPlateThreads - 1) / kPlateThreads;
     P.smem_state_floats = p->state_floats;
     P.total_modes = p->total_modes;
@@ -652,6 +706,8 @@ extern "C" int mdx_grad(mdx_plan *p, const float *exc, const double *q0, const d
         if (rc) return rc;
         // adjoint sweep over the segment
         P.mode = T.mode = MODE_REVERSE;
+        P.ring_stages = p->ring_rev;
+        P.u_slots = p->u_slots_rev;
         P.ybar = T.ybar = d_audio;
         P.adj = T.adj = w.adj;
         P.gacc = T.gacc = w.gacc;

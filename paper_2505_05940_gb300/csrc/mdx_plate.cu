@@ -105,7 +105,7 @@ __device__ __forceinline__ void consumer_bar() {
 struct Smem {
     uint64_t *full, *empty;
     float *ring;
-    float *U;      // [kChunkK][2][npad_max]
+    float *U;      // [kChunkK][u_slots][G x Npad <= kUPartFloats] row-group partial sums
     float *red;    // [2][kChunkK][4][kPlateWarps]
     float *red2;   // [2][2][kPlateWarps]
     float *state;  // item state blocks
@@ -135,13 +135,8 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
     p = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(p) + 127) & ~uintptr_t(127));
     S.ring = reinterpret_cast<float *>(p);
     p += (size_t)RING * P.stage_bytes;
-    int npad_max = 4;
-    for (int i = it0; i < it1; ++i) {
-        const int np = P.inst[P.items[i].inst].Npad;
-        npad_max = np > npad_max ? np : npad_max;
-    }
     S.U = reinterpret_cast<float *>(p);
-    p += (size_t)kChunkK * 2 * npad_max * sizeof(float);
+    p += (size_t)kChunkK * P.u_slots * kUPartFloats * sizeof(float);
     S.red = reinterpret_cast<float *>(p);
     p += (size_t)2 * kChunkK * 4 * kPlateWarps * sizeof(float);
     S.red2 = reinterpret_cast<float *>(p);
@@ -282,11 +277,19 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
         consumer_bar();
 
         // -------- phase A: coupling pass over this CTA's items
+        // Thread layout over a stage of rows (p) x columns (s) of H^k: thread
+        // (g, c) owns the float4 column strip c and the g-th contiguous block
+        // of the stage's rows.  Partial sums of the G row groups are combined
+        // through shared memory once per chunk of kChunkK stress modes.
         for (int ii = it0; ii < it1; ++ii) {
             const PlateItem item = P.items[ii];
             const InstDesc d = P.inst[item.inst];
             float *st = S.state + item.smem_state;
             const int Np = d.Npad;
+            const int ncol4 = Np >> 2;
+            const int G = max(1, min(kPlateThreads / ncol4, 32));
+            const int g = tid / ncol4, c4 = tid - (tid / ncol4) * ncol4;
+            const bool active = g < G;
             const int rows_per_stage = max(1, stage_floats / Np);
             const int nmat = (reverse && d.has_dir) ? 2 : 1;
             const float *src0 = reverse ? st + ST_SRC0 * Np : st + ST_QHI * Np;
@@ -296,15 +299,9 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                 const int nk = min(kChunkK, item.k1 - kc);
                 float *red = S.red + chunk_parity * (kChunkK * 4 * kPlateWarps);
                 for (int kk = 0; kk < nk; ++kk) {
-                    const int k = kc + kk;
-                    (void)k;
-                    float dsum[4] = {0.f, 0.f, 0.f, 0.f};
                     for (int mat = 0; mat < nmat; ++mat) {
-                        float acc[R][kMaxSpt];
-#pragma unroll
-                        for (int r = 0; r < R; ++r)
-#pragma unroll
-                            for (int j = 0; j < kMaxSpt; ++j) acc[r][j] = 0.f;
+                        float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f);
+                        float4 a1 = make_float4(0.f, 0.f, 0.f, 0.f);
                         for (int p0 = 0; p0 < d.N; p0 += rows_per_stage) {
                             const int nr = min(rows_per_stage, d.N - p0);
                             const int s = (int)(seq % RING);
@@ -314,33 +311,35 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                                 *reinterpret_cast<volatile int *>(&S.misc[1]) = 1;
                                 atomicExch((int *)gabort, 1);
                             }
-                            const float *stg = S.ring + (size_t)s * stage_floats;
-                            if (mat == 0) {
+                            if (active) {
+                                const int rpg = (nr + G - 1) / G;
+                                const int r0 = g * rpg;
+                                const int r1 = min(nr, r0 + rpg);
+                                const float *stg = S.ring + (size_t)s * stage_floats + 4 * c4;
+                                if (mat == 0 && R > 1) {
 #pragma unroll 4
-                                for (int pl = 0; pl < nr; ++pl) {
-                                    const float q0v = src0[p0 + pl];
-                                    const float q1v = (R > 1) ? src1[p0 + pl] : 0.f;
-                                    const float *row = stg + (size_t)pl * Np;
-#pragma unroll
-                                    for (int j = 0; j < kMaxSpt; ++j) {
-                                        const int sj = tid + j * kPlateThreads;
-                                        if (j < spt && sj < Np) {
-                                            const float h = row[sj];
-                                            acc[0][j] = fmaf(h, q0v, acc[0][j]);
-                                            if (R > 1) acc[R - 1][j] = fmaf(h, q1v, acc[R - 1][j]);
-                                        }
+                                    for (int r = r0; r < r1; ++r) {
+                                        const float4 h = *reinterpret_cast<const float4 *>(stg + (size_t)r * Np);
+                                        const float x = src0[p0 + r], y = src1[p0 + r];
+                                        a0.x = fmaf(h.x, x, a0.x); a0.y = fmaf(h.y, x, a0.y);
+                                        a0.z = fmaf(h.z, x, a0.z); a0.w = fmaf(h.w, x, a0.w);
+                                        a1.x = fmaf(h.x, y, a1.x); a1.y = fmaf(h.y, y, a1.y);
+                                        a1.z = fmaf(h.z, y, a1.z); a1.w = fmaf(h.w, y, a1.w);
                                     }
-                                }
-                            } else {
-                                // direction tensor: only dH q is needed
+                                } else {
+                                    // two independent chains over alternate rows
 #pragma unroll 4
-                                for (int pl = 0; pl < nr; ++pl) {
-                                    const float q0v = src0[p0 + pl];
-                                    const float *row = stg + (size_t)pl * Np;
-#pragma unroll
-                                    for (int j = 0; j < kMaxSpt; ++j) {
-                                        const int sj = tid + j * kPlateThreads;
-                                        if (j < spt && sj < Np) acc[0][j] = fmaf(row[sj], q0v, acc[0][j]);
+                                    for (int r = r0; r < r1; r += 2) {
+                                        const float4 h = *reinterpret_cast<const float4 *>(stg + (size_t)r * Np);
+                                        const float x = src0[p0 + r];
+                                        a0.x = fmaf(h.x, x, a0.x); a0.y = fmaf(h.y, x, a0.y);
+                                        a0.z = fmaf(h.z, x, a0.z); a0.w = fmaf(h.w, x, a0.w);
+                                        if (r + 1 < r1) {
+                                            const float4 h2 = *reinterpret_cast<const float4 *>(stg + (size_t)(r + 1) * Np);
+                                            const float x2 = src0[p0 + r + 1];
+                                            a1.x = fmaf(h2.x, x2, a1.x); a1.y = fmaf(h2.y, x2, a1.y);
+                                            a1.z = fmaf(h2.z, x2, a1.z); a1.w = fmaf(h2.w, x2, a1.w);
+                                        }
                                     }
                                 }
                             }
@@ -348,36 +347,65 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                             if (lane == 0) mbar_arrive(&S.empty[s]);
                             ++seq;
                         }
-                        // per-k partial dot products; keep u (and H w) for the force
-#pragma unroll
-                        for (int j = 0; j < kMaxSpt; ++j) {
-                            const int sj = tid + j * kPlateThreads;
-                            if (j < spt && sj < Np) {
-                                const float qs = src0[sj];
-                                if (mat == 0) {
-                                    float *Uk = S.U + (size_t)kk * 2 * npad_max;
-                                    Uk[sj] = acc[0][j];
-                                    dsum[0] = fmaf(qs, acc[0][j], dsum[0]);
-                                    if (R > 1) {
-                                        Uk[npad_max + sj] = acc[R - 1][j];
-                                        dsum[1] = fmaf(src1[sj], acc[0][j], dsum[1]);
-                                    }
-                                } else {
-                                    dsum[2] = fmaf(qs, acc[0][j], dsum[2]);
-                                    dsum[3] = fmaf(src1[sj], acc[0][j], dsum[3]);
-                                }
+                        if (active) {
+                            // slot 0: H q, slot 1: H w (reverse), slot 2: dH q (direction)
+                            if (mat == 0 && R > 1) {
+                                float *u0 = S.U + ((size_t)(kk * P.u_slots + 0) * G + g) * Np + 4 * c4;
+                                float *u1 = S.U + ((size_t)(kk * P.u_slots + 1) * G + g) * Np + 4 * c4;
+                                *reinterpret_cast<float4 *>(u0) = a0;
+                                *reinterpret_cast<float4 *>(u1) = a1;
+                            } else {
+                                const float4 sum = make_float4(a0.x + a1.x, a0.y + a1.y,
+                                                               a0.z + a1.z, a0.w + a1.w);
+                                float *u0 = S.U + ((size_t)(kk * P.u_slots + (mat == 0 ? 0 : 2)) * G + g) * Np + 4 * c4;
+                                *reinterpret_cast<float4 *>(u0) = sum;
                             }
                         }
                     }
+                }
+                consumer_bar();
+                // combine the row groups: u (H q), z (H w), t (dH q) for own modes
+                float uu[kChunkK][kMaxSpt], zz[kChunkK][kMaxSpt];
 #pragma unroll
-                    for (int dd = 0; dd < 4; ++dd) {
-                        const float v = warp_sum(dsum[dd]);
-                        if (lane == 0) red[(kk * 4 + dd) * kPlateWarps + warp] = v;
+                for (int kk = 0; kk < kChunkK; ++kk) {
+                    float dsum[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                    for (int j = 0; j < kMaxSpt; ++j) {
+                        uu[kk][j] = 0.f;
+                        zz[kk][j] = 0.f;
+                        const int sj = tid + j * kPlateThreads;
+                        if (kk < nk && j < spt && sj < Np) {
+                            float u = 0.f, z = 0.f, t = 0.f;
+                            for (int gg = 0; gg < G; ++gg) {
+                                u += S.U[((size_t)(kk * P.u_slots + 0) * G + gg) * Np + sj];
+                                if (R > 1) z += S.U[((size_t)(kk * P.u_slots + 1) * G + gg) * Np + sj];
+                                if (nmat > 1) t += S.U[((size_t)(kk * P.u_slots + 2) * G + gg) * Np + sj];
+                            }
+                            uu[kk][j] = u;
+                            zz[kk][j] = z;
+                            const float qs = src0[sj];
+                            dsum[0] = fmaf(qs, u, dsum[0]);
+                            if (R > 1) {
+                                const float ws = src1[sj];
+                                dsum[1] = fmaf(ws, u, dsum[1]);
+                                dsum[2] = fmaf(qs, t, dsum[2]);
+                                dsum[3] = fmaf(ws, t, dsum[3]);
+                            }
+                        }
+                    }
+                    if (kk < nk) {
+#pragma unroll
+                        for (int dd = 0; dd < 4; ++dd) {
+                            const float v = warp_sum(dsum[dd]);
+                            if (lane == 0) red[(kk * 4 + dd) * kPlateWarps + warp] = v;
+                        }
                     }
                 }
                 consumer_bar();
                 // chunk epilogue: reduce the dot products, accumulate the forces
-                for (int kk = 0; kk < nk; ++kk) {
+#pragma unroll
+                for (int kk = 0; kk < kChunkK; ++kk) {
+                    if (kk >= nk) break;
                     const int k = kc + kk;
                     float dv[4];
 #pragma unroll
@@ -388,17 +416,20 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                         dv[dd] = a;
                     }
                     const float kap = P.kappa[d.k_off + k];
-                    const float *Uk = S.U + (size_t)kk * 2 * npad_max;
-                    for (int s = tid; s < Np; s += kPlateThreads) {
-                        const float u = Uk[s];
-                        if (!reverse) {
-                            st[ST_FLOC * Np + s] = fmaf(kap * dv[0], u, st[ST_FLOC * Np + s]);
-                        } else {
-                            const float z = Uk[npad_max + s];
-                            // f = sum kappa eta u ; J w = sum kappa (2 xi u + eta z)
-                            st[ST_FLOC2 * Np + s] = fmaf(kap * dv[0], u, st[ST_FLOC2 * Np + s]);
-                            st[ST_FLOC * Np + s] =
-                                fmaf(kap, fmaf(2.f * dv[1], u, dv[0] * z), st[ST_FLOC * Np + s]);
+#pragma unroll
+                    for (int j = 0; j < kMaxSpt; ++j) {
+                        const int sj = tid + j * kPlateThreads;
+                        if (j < spt && sj < Np) {
+                            const float u = uu[kk][j];
+                            if (!reverse) {
+                                st[ST_FLOC * Np + sj] = fmaf(kap * dv[0], u, st[ST_FLOC * Np + sj]);
+                            } else {
+                                const float z = zz[kk][j];
+                                // f = sum kappa eta u ; J w = sum kappa (2 xi u + eta z)
+                                st[ST_FLOC2 * Np + sj] = fmaf(kap * dv[0], u, st[ST_FLOC2 * Np + sj]);
+                                st[ST_FLOC * Np + sj] =
+                                    fmaf(kap, fmaf(2.f * dv[1], u, dv[0] * z), st[ST_FLOC * Np + sj]);
+                            }
                         }
                     }
                     if (reverse && tid == 0) {
@@ -590,11 +621,11 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
     }
 }
 
-size_t plate_smem_bytes(int ring_stages, int stage_bytes, int npad_max, int state_floats) {
+size_t plate_smem_bytes(int ring_stages, int stage_bytes, int u_slots, int state_floats) {
     size_t b = 2 * ring_stages * sizeof(uint64_t) + 16 * sizeof(int);
     b = (b + 127) & ~size_t(127);
     b += (size_t)ring_stages * stage_bytes;
-    b += (size_t)kChunkK * 2 * npad_max * sizeof(float);
+    b += (size_t)kChunkK * u_slots * kUPartFloats * sizeof(float);
     b += (size_t)2 * kChunkK * 4 * kPlateWarps * sizeof(float);
     b += (size_t)2 * 2 * kPlateWarps * sizeof(float);
     b += (size_t)state_floats * sizeof(float);

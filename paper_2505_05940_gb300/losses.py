@@ -28,8 +28,10 @@ def log_stft_l1(y, target, n_fft, eps=1e-5):
 
 
 def multires_log_stft(y, target, n_ffts=(256, 1024, 4096), eps=1e-5):
-    """Per-instance sum over resolutions of the mean log-magnitude L1 (Eq. 24)."""
-    return sum(log_stft_l1(y, target, n, eps) for n in n_ffts)
+    """Per-instance sum over resolutions of the mean log-magnitude L1 (Eq. 24).
+    Resolutions longer than half the signal are skipped (reflect padding)."""
+    usable = [n for n in n_ffts if n // 2 < y.shape[-1]] or [min(n_ffts)]
+    return sum(log_stft_l1(y, target, n, eps) for n in usable)
 
 
 def spectral_convergence(y, target, n_fft=1024):
