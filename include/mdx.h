@@ -216,6 +216,34 @@ int mdx_coeffs_vjp(int n, const double *lambda, double D, double T0, double rho,
                    double s1, const double *d_omega2, const double *d_gamma, double *dD,
                    double *dT0, double *ds0, double *ds1, double *d_lambda);
 
+/*
+ * Forward run of strings and membranes that allocates no device memory.
+ * The paper has no counterpart: this entry point exists for callers that must
+ * not call cudaMalloc, such as a real-time audio callback (cudaMalloc can
+ * block for milliseconds and synchronises the device) or a plug-in whose host
+ * application owns every device buffer.  It computes the same forward pass as
+ * mdx_plan_create + mdx_simulate for MDX_KIND_TENSION instances, without a plan.
+ *   inst     [n_inst] host descriptions, all MDX_KIND_TENSION (H, kappa, dH unused)
+ *   exc      device [n_inst][steps] FP32 excitation (NULL = zero)
+ *   q0, qm1  device [total_modes] FP64 initial state (NULL = zero)
+ *   audio    device [n_inst][steps] FP32 output (NULL = not written)
+ *   q_end, qm1_end  device [total_modes] FP64 final state (NULL = skip)
+ *   status   device [n_inst] int, as in mdx_simulate (NULL = not written)
+ * Scratch: one fixed 1 MiB block of device memory per GPU, owned by the
+ * library (a file-scope __device__ array held until the process exits).  It
+ * bounds the problem: total modes <= (1 MiB - 76 B x n_inst) / 44 B (about
+ * 23 800 modes for one instance); larger requests fail with MDX_ERR_UNSUPPORTED.  No call
+ * allocates or frees device memory.  The first call on a device looks up the
+ * block's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Every call reuses the same
+ * block: calls that overlap on the GPU (e.g. on two streams) race and must
+ * be serialised.  Errors: MDX_ERR_ARG, MDX_ERR_UNSTABLE, MDX_ERR_NONFINITE,
+ * MDX_ERR_UNSUPPORTED, MDX_ERR_CUDA (message in mdx_last_error).
+ */
+int mdx_simulate_strings_noalloc(const mdx_instance *inst, int n_inst, const float *exc,
+                                 const double *q0, const double *qm1, int steps, float *audio,
+                                 double *q_end, double *qm1_end, int *status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -157,6 +157,9 @@ struct TensionParams {
     int *status;
 };
 
+// Sets the thread-local message returned by mdx_last_error; returns code.
+int set_last_error(int code, const char *msg);
+
 // Launchers (defined in the kernel translation units).
 size_t plate_smem_bytes(int ring_stages, int stage_bytes, int u_slots, int state_floats);
 cudaError_t launch_plate(const PlateParams &p, int grid, size_t smem, cudaStream_t s);

@@ -50,6 +50,8 @@ struct DevBuf {
 
 }  // namespace
 
+int mdx::set_last_error(int code, const char *msg) { return fail(code, "%s", msg); }
+
 struct mdx_plan {
     int device = 0;
     int n_inst = 0;
