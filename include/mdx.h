@@ -189,6 +189,18 @@ int mdx_grad(mdx_plan *plan, const float *exc, const double *q0, const double *q
              size_t work_bytes, const mdx_grads *out, int *status, void *stream);
 
 /*
+ * Tile configuration of the plate kernel (used by the autotuner): TMA stage
+ * size in bytes (multiple of 16, 0 = default 64 KB) and ring depth (0 = as
+ * many stages as shared memory allows).  Takes effect for later launches;
+ * fails with MDX_ERR_UNSUPPORTED if the stages do not fit in shared memory.
+ * mdx_plan_tiles reports the current stage size, ring depths of the forward
+ * and reverse launches, and the number of persistent CTAs.
+ */
+int mdx_plan_configure(mdx_plan *plan, int stage_bytes, int ring_stages);
+int mdx_plan_tiles(const mdx_plan *plan, int *stage_bytes, int *ring_fwd, int *ring_rev,
+                   int *ctas);
+
+/*
  * Kernel timing (tracing).  When enabled, every plate-kernel launch of the
  * plan is bracketed by CUDA events on its launch stream.  mdx_plan_kernel_stats
  * synchronises those events and returns, for one launch class

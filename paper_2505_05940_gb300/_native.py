@@ -25,7 +25,8 @@ _ERRORS = {
 EXPORTED = ("mdx_last_error", "mdx_version", "mdx_plan_create", "mdx_plan_destroy",
             "mdx_plan_info", "mdx_checkpoint_bytes", "mdx_simulate", "mdx_grad_workspace_bytes",
             "mdx_grad", "mdx_coeffs_from_physics", "mdx_coeffs_vjp", "mdx_plan_set_profiling",
-            "mdx_plan_kernel_stats", "mdx_plan_reset_stats")
+            "mdx_plan_kernel_stats", "mdx_plan_reset_stats", "mdx_plan_configure",
+            "mdx_plan_tiles", "mdx_simulate_strings_noalloc")
 
 
 class MdxError(RuntimeError):
@@ -94,6 +95,8 @@ def load(build_if_missing: bool = True):
                                               _D, _D]
         L.mdx_coeffs_vjp.argtypes = [i32, _D, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, _D, _D, _D, _D, _D, _D, _D]
+        L.mdx_plan_configure.argtypes = [vp, i32, i32]
+        L.mdx_plan_tiles.argtypes = [vp] + [ctypes.POINTER(i32)] * 4
         L.mdx_plan_set_profiling.argtypes = [vp, i32]
         L.mdx_plan_reset_stats.argtypes = [vp]
         L.mdx_plan_kernel_stats.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_long),
@@ -202,6 +205,16 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    # ------------------------------------------------------------------ tiles
+    def configure(self, stage_bytes=0, ring_stages=0):
+        check(load().mdx_plan_configure(self._h, int(stage_bytes), int(ring_stages)))
+
+    def tiles(self):
+        v = [ctypes.c_int() for _ in range(4)]
+        check(load().mdx_plan_tiles(self._h, *[ctypes.byref(x) for x in v]))
+        return dict(stage_bytes=v[0].value, ring_fwd=v[1].value, ring_rev=v[2].value,
+                    ctas=v[3].value)
 
     # ------------------------------------------------------------------ tracing
     def set_profiling(self, enable=True):

@@ -163,6 +163,7 @@ int set_last_error(int code, const char *msg);
 // Launchers (defined in the kernel translation units).
 size_t plate_smem_bytes(int ring_stages, int stage_bytes, int u_slots, int state_floats);
 cudaError_t launch_plate(const PlateParams &p, int grid, size_t smem, cudaStream_t s);
+cudaError_t plate_set_smem_limit(size_t smem);
 cudaError_t launch_tension(const TensionParams &p, int max_n, cudaStream_t s);
 
 struct AuxInit {

@@ -97,6 +97,7 @@ struct mdx_plan {
     long stat_launch[3] = {0, 0, 0};
     double stat_ms[3] = {0, 0, 0}, stat_bytes[3] = {0, 0, 0};
     double H_bytes_per_step = 0, dH_bytes_per_step = 0;
+    int smem_optin = 0;
 };
 
 namespace {
@@ -183,6 +184,8 @@ struct Piece {
     int inst, k0, k1;
     double cost;
 };
+
+int configure_tiles(mdx_plan *p, int stage_req, int ring_req);
 
 }  // namespace
 
@@ -476,38 +479,10 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
         p->n_cta = (int)cta_off.size() - 1;
         p->state_floats = max_state;
         // ring: stages of >= one padded row, filling the remaining shared memory
-        // default stage: 64 KB (fewer ring turnovers per byte), halved until
-        // at least two stages fit beside the reverse sweep's buffers
-        int stage = o.stage_bytes > 0 ? o.stage_bytes : 64 * 1024;
-        stage = std::max(stage, p->npad_max * 4);
-        stage = (stage + 15) & ~15;
-        if (o.stage_bytes <= 0) {
-            while (stage > 16 * 1024 && stage / 2 >= p->npad_max * 4 &&
-                   plate_smem_bytes(2, stage, 3, p->state_floats) + 1024 > (size_t)smem_optin)
-                stage = ((stage / 2) + 15) & ~15;
-        }
-        p->stage_bytes = stage;
-        bool dir = false;
-        for (const auto &d : p->inst) dir = dir || d.has_dir;
-        p->u_slots_fwd = 1;
-        p->u_slots_rev = dir ? 3 : 2;
-        for (int which = 0; which < 2; ++which) {
-            const int us = which == 0 ? p->u_slots_fwd : p->u_slots_rev;
-            const size_t fixed = plate_smem_bytes(0, stage, us, p->state_floats);
-            if (fixed + 2 * (size_t)stage + 1024 > (size_t)smem_optin)
-                return bail(fail(MDX_ERR_UNSUPPORTED,
-                                 "plate kernel needs %zu B of shared memory (> %d)",
-                                 fixed + 2 * (size_t)stage, smem_optin));
-            int ring = o.ring_stages > 0 ? o.ring_stages
-                                         : (int)((size_t)(smem_optin - 1024 - fixed) / stage);
-            ring = std::max(2, std::min(ring, 16));
-            const size_t need = plate_smem_bytes(ring, stage, us, p->state_floats);
-            if (need > (size_t)smem_optin)
-                return bail(fail(MDX_ERR_UNSUPPORTED,
-                                 "plate kernel needs %zu B of shared memory (> %d)", need,
-                                 smem_optin));
-            (which == 0 ? p->ring_fwd : p->ring_rev) = ring;
-            (which == 0 ? p->smem_fwd : p->smem_rev) = need;
+        p->smem_optin = smem_optin;
+        {
+            const int rcc = configure_tiles(p, o.stage_bytes, o.ring_stages);
+            if (rcc) return bail(rcc);
         }
         int rc;
         if ((rc = upload(p, &p->d_items, items.data(), items.size()))) return bail(rc);
@@ -533,6 +508,50 @@ size_t mdx_checkpoint_bytes(const mdx_plan *p, int steps, int K) {
 }  // extern "C"
 
 namespace {
+
+// Ring geometry: stage size (default 64 KB, halved while two stages do not fit
+// beside the reverse sweep's buffers) and as many stages as shared memory
+// allows, separately for the forward and the reverse launch.
+int configure_tiles(mdx_plan *p, int stage_req, int ring_req) {
+    const int smem_optin = p->smem_optin;
+    int stage = stage_req > 0 ? stage_req : 64 * 1024;
+    stage = std::max(stage, p->npad_max * 4);
+    stage = (stage + 15) & ~15;
+    if (stage_req <= 0) {
+        while (stage > 16 * 1024 && stage / 2 >= p->npad_max * 4 &&
+               plate_smem_bytes(2, stage, 3, p->state_floats) + 1024 > (size_t)smem_optin)
+            stage = ((stage / 2) + 15) & ~15;
+    }
+    bool dir = false;
+    for (const auto &d : p->inst) dir = dir || d.has_dir;
+    const int us_fwd = 1, us_rev = dir ? 3 : 2;
+    int ring_f = 0, ring_r = 0;
+    size_t smem_f = 0, smem_r = 0;
+    for (int which = 0; which < 2; ++which) {
+        const int us = which == 0 ? us_fwd : us_rev;
+        const size_t fixed = plate_smem_bytes(0, stage, us, p->state_floats);
+        if (fixed + 2 * (size_t)stage + 1024 > (size_t)smem_optin)
+            return fail(MDX_ERR_UNSUPPORTED, "plate kernel needs %zu B of shared memory (> %d)",
+                        fixed + 2 * (size_t)stage, smem_optin);
+        int ring = ring_req > 0 ? ring_req : (int)((size_t)(smem_optin - 1024 - fixed) / stage);
+        ring = std::max(2, std::min(ring, 16));
+        const size_t need = plate_smem_bytes(ring, stage, us, p->state_floats);
+        if (need > (size_t)smem_optin)
+            return fail(MDX_ERR_UNSUPPORTED, "plate kernel needs %zu B of shared memory (> %d)",
+                        need, smem_optin);
+        (which == 0 ? ring_f : ring_r) = ring;
+        (which == 0 ? smem_f : smem_r) = need;
+    }
+    MDX_CUDA(plate_set_smem_limit(std::max(smem_f, smem_r)), "cudaFuncSetAttribute");
+    p->stage_bytes = stage;
+    p->u_slots_fwd = us_fwd;
+    p->u_slots_rev = us_rev;
+    p->ring_fwd = ring_f;
+    p->ring_rev = ring_r;
+    p->smem_fwd = smem_f;
+    p->smem_rev = smem_r;
+    return MDX_OK;
+}
 
 PlateParams base_plate(mdx_plan *p, int mode, int steps, int n_begin, int total_steps) {
     PlateParams P{};
@@ -818,5 +837,24 @@ extern "C" int mdx_plan_kernel_stats(mdx_plan *p, int which, long *launches, dou
     if (launches) *launches = p->stat_launch[which];
     if (ms) *ms = p->stat_ms[which];
     if (bytes) *bytes = p->stat_bytes[which];
+    return MDX_OK;
+}
+
+extern "C" int mdx_plan_configure(mdx_plan *p, int stage_bytes, int ring_stages) {
+    if (!p) return fail(MDX_ERR_ARG, "plan is NULL");
+    if (stage_bytes < 0 || ring_stages < 0 || (stage_bytes % 16) != 0)
+        return fail(MDX_ERR_ARG, "stage_bytes must be a non-negative multiple of 16");
+    if (!p->any_plate) return MDX_OK;
+    MDX_CUDA(cudaSetDevice(p->device), "cudaSetDevice");
+    return configure_tiles(p, stage_bytes, ring_stages);
+}
+
+extern "C" int mdx_plan_tiles(const mdx_plan *p, int *stage_bytes, int *ring_fwd, int *ring_rev,
+                              int *ctas) {
+    if (!p) return fail(MDX_ERR_ARG, "plan is NULL");
+    if (stage_bytes) *stage_bytes = p->stage_bytes;
+    if (ring_fwd) *ring_fwd = p->ring_fwd;
+    if (ring_rev) *ring_rev = p->ring_rev;
+    if (ctas) *ctas = p->n_cta;
     return MDX_OK;
 }

@@ -632,22 +632,31 @@ size_t plate_smem_bytes(int ring_stages, int stage_bytes, int u_slots, int state
     return b;
 }
 
+cudaError_t plate_set_smem_limit(size_t smem) {
+    cudaError_t e = cudaFuncSetAttribute(plate_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(plate_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+}
+
+// Cooperative launch (all CTAs resident: the per-plate exchange waits on
+// other CTAs) through cudaLaunchKernelEx, which is also valid inside stream
+// capture.
 cudaError_t launch_plate(const PlateParams &p, int grid, size_t smem, cudaStream_t s) {
     if (grid <= 0) return cudaSuccess;
-    void *args[] = {const_cast<PlateParams *>(&p)};
-    cudaError_t e;
-    if (p.mode == MODE_REVERSE) {
-        e = cudaFuncSetAttribute(plate_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e != cudaSuccess) return e;
-        return cudaLaunchCooperativeKernel((const void *)plate_kernel<2>, dim3(grid),
-                                           dim3(kPlateBlock), args, smem, s);
-    }
-    e = cudaFuncSetAttribute(plate_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaLaunchCooperativeKernel((const void *)plate_kernel<1>, dim3(grid),
-                                       dim3(kPlateBlock), args, smem, s);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kPlateBlock);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (p.mode == MODE_REVERSE) return cudaLaunchKernelEx(&cfg, plate_kernel<2>, p);
+    return cudaLaunchKernelEx(&cfg, plate_kernel<1>, p);
 }
 
 }  // namespace mdx

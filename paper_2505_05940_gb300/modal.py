@@ -105,6 +105,61 @@ class Simulator:
         return out
 
 
+    # ------------------------------------------------------------------ CUDA graphs
+    def capture(self, steps, K=0, with_grad=False):
+        """Capture one forward call (and, with with_grad, the adjoint with a
+        fixed dL/dy buffer) into a CUDA graph.  Returns a GraphRun whose
+        replay() re-executes the whole captured sequence with one launch from
+        the host; inputs are read from, and outputs written to, the static
+        buffers of the GraphRun (copy new inputs into them before replay)."""
+        return GraphRun(self, steps, K, with_grad)
+
+
+class GraphRun:
+    def __init__(self, sim, steps, K, with_grad):
+        dev = sim.device
+        self.sim, self.steps, self.K = sim, steps, K
+        self.exc = sim._exc_for(steps).clone()
+        self.q0 = sim.q0.detach().clone()
+        self.qm1 = sim.qm1.detach().clone()
+        self.audio = torch.empty(sim.n_inst, steps, dtype=torch.float32, device=dev)
+        self.ckpt = None
+        if K > 0:
+            self.ckpt = torch.empty(sim.plan.checkpoint_bytes(steps, K) // 4, dtype=torch.float32,
+                                    device=dev)
+        self.d_audio = self.grads = self.work = None
+        if with_grad:
+            assert K > 0, "the adjoint needs checkpoints (K > 0)"
+            self.d_audio = torch.zeros(sim.n_inst, steps, dtype=torch.float32, device=dev)
+            self.work = torch.empty(sim.plan.workspace_bytes(steps, K) // 4 + 1,
+                                    dtype=torch.float32, device=dev)
+            f64 = dict(dtype=torch.float64, device=dev)
+            TM = sim.total_modes
+            self.grads = dict(d_omega2=torch.empty(TM, **f64), d_gamma=torch.empty(TM, **f64),
+                              d_b=torch.empty(TM, **f64), d_c=torch.empty(TM, **f64),
+                              d_q0=torch.empty(TM, **f64), d_qm1=torch.empty(TM, **f64),
+                              d_tau=torch.empty(sim.n_inst, **f64),
+                              d_kappa=torch.empty(max(1, sim.kappa.numel()), **f64),
+                              d_dir=torch.empty(sim.n_inst, **f64))
+        self._body()                       # warm-up outside capture
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self._body()
+
+    def _body(self):
+        sim = self.sim
+        sim.plan.simulate(self.steps, exc=self.exc, q0=self.q0, qm1=self.qm1, K=self.K,
+                          ckpt=self.ckpt, audio=self.audio)
+        if self.grads is not None:
+            sim.plan.grad(self.steps, self.d_audio, self.K, self.ckpt, self.work, exc=self.exc,
+                          out=self.grads)
+
+    def replay(self):
+        self.graph.replay()
+        return self.audio
+
+
 class _SimulateFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, sim, steps, K, omega2, gamma, b, c, tau, kappa, q0, qm1, direction):

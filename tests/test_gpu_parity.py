@@ -212,3 +212,44 @@ def test_bounded_wait_reports_timeout_and_context_survives():
                               debug_flags=1)
     assert status[0] == 4
     check_parity([oi], wl.fs, wl.steps, force_split=2)
+
+
+def test_cuda_graph_replay_matches_direct_calls():
+    """A ragged batch captured once in a CUDA graph (forward + adjoint) and
+    replayed gives bit-identical audio and gradients to direct calls."""
+    fs, steps = 44100.0, 600
+    insts = [W.tiny_random(40, "plate", 48, 12, steps=steps).instances[0],
+             W.tiny_random(41, "membrane", 60, steps=steps).instances[0],
+             W.tiny_random(42, "plate", 30, 7, steps=steps).instances[0]]
+    ois = [oracle_instance(i, fs, steps) for i in insts]
+    sim = modal.Simulator([to_plan(o, fs) for o in ois])
+    K = 128
+    run = sim.capture(steps, K=K, with_grad=True)
+    yb = torch.randn(len(ois), steps, device="cuda")
+    run.d_audio.copy_(yb)
+    for _ in range(2):
+        audio = run.replay().clone()
+    torch.cuda.synchronize()
+    direct = sim.simulate(steps, K=K)
+    g = sim.grad(steps, yb, K, direct["ckpt"])
+    torch.cuda.synchronize()
+    assert torch.equal(audio, direct["audio"])
+    for k in ("d_omega2", "d_gamma", "d_kappa"):
+        assert torch.equal(run.grads[k][:g[k].numel()], g[k]), k
+
+
+def test_autotuner_picks_a_fitting_stage_and_keeps_parity(tmp_path):
+    from paper_2505_05940_gb300 import autotune
+    wl = W.tiny_random(50, "plate", 96, 24, steps=500)
+    wl.instances[0].F0 = 300.0
+    oi = oracle_instance(wl.instances[0], wl.fs, wl.steps)
+    sim = modal.Simulator([to_plan(oi, wl.fs)])
+    res = autotune.tune(sim, steps=64, cache_path=str(tmp_path / "tune.json"))
+    assert res["stage_bytes"] in autotune.STAGE_CANDIDATES and not res["cached"]
+    assert sim.plan.tiles()["stage_bytes"] == res["stage_bytes"]
+    again = autotune.tune(sim, steps=64, cache_path=str(tmp_path / "tune.json"))
+    assert again["cached"] and again["stage_bytes"] == res["stage_bytes"]
+    r = sim.simulate(wl.steps)
+    torch.cuda.synchronize()
+    ref = oracle.forward(oi)["y"]
+    assert rel(r["audio"].cpu().numpy()[0], ref) <= TOL
