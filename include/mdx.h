@@ -74,6 +74,15 @@ extern "C" {
  *   kappa    [M] kappa_k = E / (2 rho zeta_k^4) (Eq. 9)
  *   dH       optional [M][N][N] FP32 direction tensor (e.g. dH/d aspect) for
  *            mdx_grad's directional derivative <dL/dH, dH>; NULL if unused
+ *   phi_class, psi_class  optional [N] and [M] symmetry classes in 0..3 (plate).
+ *            For a simply supported rectangle, L(Phi_i, Phi_j) (Eq. 7) is odd
+ *            about a mid-line when exactly one of Phi_i, Phi_j is, so H^k_ij
+ *            (Eq. 10) vanishes unless phi_class[i] ^ phi_class[j] == psi_class[k]
+ *            (bit 1: odd about x = Lx/2, bit 0: odd about y = Ly/2).  When
+ *            every plate of a plan gives classes, the plan stores and streams
+ *            only the nonzero class blocks (a quarter of H).  The plan checks
+ *            the pattern: an entry outside it larger than 1e-6 max|H^k| fails
+ *            with MDX_ERR_ARG; smaller ones are treated as zero.
  * Stability: every mode needs omega_mu * dt < 2 (Eq. 20 is explicit);
  * otherwise mdx_plan_create fails with MDX_ERR_UNSTABLE naming the mode.
  */
@@ -91,6 +100,8 @@ typedef struct mdx_instance {
     const float *H;
     const double *kappa;
     const float *dH;
+    const int *phi_class;
+    const int *psi_class;
 } mdx_instance;
 
 /* Plan options; zero-initialise for defaults. */

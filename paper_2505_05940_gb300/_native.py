@@ -42,7 +42,9 @@ _F = ctypes.POINTER(ctypes.c_float)
 class Instance(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("n_phi", ctypes.c_int), ("n_psi", ctypes.c_int),
                 ("dt", ctypes.c_double), ("omega2", _D), ("gamma", _D), ("b", _D), ("c", _D),
-                ("lambda_", _D), ("tau", ctypes.c_double), ("H", _F), ("kappa", _D), ("dH", _F)]
+                ("lambda_", _D), ("tau", ctypes.c_double), ("H", _F), ("kappa", _D), ("dH", _F),
+                ("phi_class", ctypes.POINTER(ctypes.c_int)),
+                ("psi_class", ctypes.POINTER(ctypes.c_int))]
 
 
 class Options(ctypes.Structure):
@@ -139,7 +141,7 @@ class Plan:
     """
 
     def __init__(self, instances, device=0, max_ctas=0, ring_stages=0, stage_bytes=0,
-                 force_split=0, wait_limit=0, debug_flags=0):
+                 force_split=0, wait_limit=0, debug_flags=0, use_classes=True):
         L = load()
         self._keep = []
         arr = (Instance * len(instances))()
@@ -161,6 +163,11 @@ class Plan:
                 self._keep.append(a)
                 return a.ctypes.data_as(_F)
 
+            def iptr(x):
+                a = np.ascontiguousarray(x, dtype=np.int32)
+                self._keep.append(a)
+                return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
             s.omega2, s.gamma, s.b, s.c = (dptr(d[k]) for k in ("omega2", "gamma", "b", "c"))
             if kind == KIND_TENSION:
                 s.lambda_ = dptr(d["lam"])
@@ -174,6 +181,10 @@ class Plan:
                     s.kappa = dptr(d["kappa"])
                     if d.get("dH") is not None:
                         s.dH = fptr(d["dH"])
+                    if (d.get("phi_class") is not None and d.get("psi_class") is not None
+                            and use_classes):
+                        s.phi_class = iptr(d["phi_class"])
+                        s.psi_class = iptr(d["psi_class"])
                 else:
                     s.n_psi = 0
         opts = Options(device, max_ctas, ring_stages, stage_bytes, force_split, wait_limit,

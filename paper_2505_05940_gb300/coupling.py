@@ -129,6 +129,29 @@ def coupling_tensor(Lx, Ly, labels, n_psi, n_basis=None, n_quad=None, airy=None)
     return H, zeta4
 
 
+def transverse_classes(labels):
+    """Symmetry class of each simply supported mode sin(m pi x/Lx) sin(n pi y/Ly):
+    bit 1 set when the mode is odd about x = Lx/2 (m even), bit 0 when odd
+    about y = Ly/2 (n even)."""
+    labels = np.asarray(labels, dtype=np.int64)
+    return (2 * ((labels[:, 0] + 1) % 2) + ((labels[:, 1] + 1) % 2)).astype(np.int32)
+
+
+def airy_classes(C):
+    """Symmetry class of each Airy mode from its Ritz coefficients: the basis
+    B_a(x) B_b(y) is odd about the x mid-line for odd a and about the y
+    mid-line for odd b, and every eigenvector lives in one parity block."""
+    nb = C.shape[1]
+    par = np.arange(nb) % 2
+    out = []
+    for Ck in C:
+        w = np.abs(Ck)
+        ax = int(np.argmax([w[par == 0].sum(), w[par == 1].sum()]))
+        ay = int(np.argmax([w[:, par == 0].sum(), w[:, par == 1].sum()]))
+        out.append(2 * ax + ay)
+    return np.array(out, dtype=np.int32)
+
+
 def sides(area, aspect):
     return math.sqrt(area / aspect), math.sqrt(area * aspect)
 
@@ -142,14 +165,24 @@ def coupling_with_aspect_derivative(area, aspect, labels, n_psi, rel_step=1e-4, 
     z0, C0 = airy_modes(Lx, Ly, n_psi, nb)
     H0, _ = coupling_tensor(Lx, Ly, labels, n_psi, nb, airy=(z0, C0))
     h = rel_step * aspect
+    cls0 = airy_classes(C0)
     out = []
     for a in (aspect + h, aspect - h):
         lx, ly = sides(area, a)
-        z, C = airy_modes(lx, ly, n_psi, nb)
+        # a few extra modes so that a crossing at the cut cannot lose a partner
+        z, C = airy_modes(lx, ly, n_psi + 4, nb)
+        cls = airy_classes(C)
+        # pair every mode at `aspect` with the mode of the same symmetry class
+        # whose eigenvalue is closest (robust to ordering changes), then align signs
+        order = []
+        for k in range(n_psi):
+            cand = [j for j in range(len(z)) if cls[j] == cls0[k] and j not in order]
+            order.append(min(cand, key=lambda j: abs(z[j] - z0[k])))
+        z, C = z[order], C[order]
         sgn = np.sign(np.einsum("kab,kab->k", C, C0))
         C = C * sgn[:, None, None]
         Ha, _ = coupling_tensor(lx, ly, labels, n_psi, nb, airy=(z, C))
         out.append((Ha, z))
     dH = (out[0][0] - out[1][0]) / (2 * h)
     dz = (out[0][1] - out[1][1]) / (2 * h)
-    return H0, z0, dH, dz
+    return H0, z0, dH, dz, airy_classes(C0)

@@ -101,7 +101,7 @@ __global__ void grad_epilogue_kernel(const GradEpilogue g) {
         if (g.d_tau) g.d_tau[i] = (d.kind == 0 && g.tacc) ? kval(g.tacc + 2 * i) : 0.0;
         double dir = 0.0;
         for (int k = 0; k < d.M; ++k) {
-            if (g.d_kappa) g.d_kappa[d.k_off + k] = kval(g.kacc + 2 * (d.k_off + k));
+            if (g.d_kappa) g.d_kappa[d.k_off + g.kperm[d.k_off + k]] = kval(g.kacc + 2 * (d.k_off + k));
             if (d.has_dir) dir += kval(g.diracc + 2 * (d.k_off + k));
         }
         if (g.d_dir) g.d_dir[i] = dir;

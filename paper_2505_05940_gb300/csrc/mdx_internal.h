@@ -27,6 +27,8 @@ constexpr int kStateArrays = 4;      // q_hi, q_lo, v_hi, v_lo
 constexpr int kMaxSpt = 4;             // modes per consumer thread (N_pad <= 1024)
 constexpr int kChunkK = 4;             // stress modes reduced together
 constexpr int kUPartFloats = 1024;     // row groups x N_pad <= 256 threads x 4 columns
+constexpr int kParQmax = 2;            // parity layout: column quads per thread
+constexpr int kParMcMax = 16;          // parity layout: stress modes per chunk
 constexpr int kTensionWarpsPerBlock = 4;
 constexpr int kTensionMaxJ = 32;       // modes per lane (N <= 1024)
 
@@ -60,6 +62,21 @@ struct InstDesc {
     long long part_off; // plate: first exchange slot (slots are [n_contrib][3][Npad])
     int has_dir;        // plate: a direction tensor dH is present
     long long dH_off;   // float offset of dH^0 (same layout as H)
+    // symmetry-class layout (parity != 0): transverse modes in class order
+    int parity;
+    int ncls[4];        // transverse modes per class
+    int ocls[4];        // first class-ordered position of each class
+    long long perm_off; // perm[perm_off + class position] = mode index within the instance
+};
+
+// One class chunk of a plate item (parity layout): mc consecutive internal
+// stress modes, all of class c, starting at internal index kl0.  Its coupling
+// data is four super-blocks a = 0..3 (rows p of class a, columns s of class
+// b = a ^ c), each stored as [p][k in chunk][s padded to 4] at float offset
+// off (H) and doff (dH).
+struct ParityChunk {
+    int c, kl0, mc, pad;
+    long long off, doff;
 };
 
 // One contiguous range of stress modes of one plate, processed by one CTA.
@@ -69,6 +86,7 @@ struct PlateItem {
     int slot;           // this CTA's index among the instance's contributors
     int owner;          // 1: this CTA writes audio / state / gradients of the instance
     int smem_state;     // float offset of this item's state block in shared memory
+    int chunk0, chunk1; // parity layout: the item's class chunks
 };
 
 // Shared-memory state block of one item (floats, each of length Npad).
@@ -77,6 +95,7 @@ enum StateArr : int {
     ST_FLOC,                        // local partial force (forward) / J w (reverse)
     ST_SRC0, ST_SRC1,               // right-hand sides of the H pass (reverse: q^n, w)
     ST_FLOC2,                       // reverse: local partial force at q^n
+    ST_QP, ST_WP,                   // parity layout: right-hand sides in class order
     ST_NARR
 };
 
@@ -110,6 +129,11 @@ struct PlateParams {
     int stage_bytes;
     int ring_stages;
     int u_slots;                  // row-group partial-sum slots: 1 forward, 2-3 reverse
+    int u_floats;                 // floats of the partial-sum region
+    int parity;                   // 1: coupling in symmetry-class chunks
+    int npad_max;                 // parity layout: row stride of the per-chunk u buffer
+    const ParityChunk *chunks;
+    const int *perm;
     int max_spt;
     int smem_state_floats;
     // forward I/O
@@ -161,7 +185,7 @@ struct TensionParams {
 int set_last_error(int code, const char *msg);
 
 // Launchers (defined in the kernel translation units).
-size_t plate_smem_bytes(int ring_stages, int stage_bytes, int u_slots, int state_floats);
+size_t plate_smem_bytes(int ring_stages, int stage_bytes, int u_floats, int state_floats);
 cudaError_t launch_plate(const PlateParams &p, int grid, size_t smem, cudaStream_t s);
 cudaError_t plate_set_smem_limit(size_t smem);
 cudaError_t launch_tension(const TensionParams &p, int max_n, cudaStream_t s);
@@ -185,6 +209,7 @@ struct GradEpilogue {
     long long total_modes, total_k;
     const double *omega2, *gamma, *dt;  // per mode FP64
     const float *adj, *gacc, *kacc, *diracc, *tacc;
+    const int *kperm;                   // internal stress index -> user index (per plate)
     double *d_omega2, *d_gamma, *d_b, *d_c, *d_q0, *d_qm1, *d_tau, *d_kappa, *d_dir;
 };
 cudaError_t launch_grad_epilogue(const GradEpilogue &g, int max_n, cudaStream_t s);

@@ -72,6 +72,7 @@ struct mdx_plan {
     int npad_max = 4;
     int state_floats = 0;
     int ring_fwd = 0, ring_rev = 0, stage_bytes = 0, u_slots_fwd = 1, u_slots_rev = 2;
+    int u_floats_fwd = 0, u_floats_rev = 0;
     size_t smem_fwd = 0, smem_rev = 0;
     long long part_stride = 0;
     float *d_part = nullptr;
@@ -98,6 +99,12 @@ struct mdx_plan {
     double stat_ms[3] = {0, 0, 0}, stat_bytes[3] = {0, 0, 0};
     double H_bytes_per_step = 0, dH_bytes_per_step = 0;
     int smem_optin = 0;
+    // symmetry-class layout
+    bool parity = false;
+    int mc_max = kParMcMax;
+    int min_stage_floats = 4;
+    ParityChunk *d_chunks = nullptr;
+    int *d_perm = nullptr, *d_kperm = nullptr;
 };
 
 namespace {
@@ -244,11 +251,8 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
     // ---- per-instance layout and FP64 -> FP32 coefficients (difference form)
     std::vector<float> eps, rw2, rw2lo, r, b, c, lam;
     std::vector<double> w2d, gmd, dtd;
-    std::vector<float> kap;
-    long long H_total = 0;
     p->inst.resize(n_inst);
     p->dt.resize(n_inst);
-    bool any_dir = false;
     for (int i = 0; i < n_inst; ++i) {
         const mdx_instance &S = I[i];
         InstDesc d{};
@@ -259,10 +263,7 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
         d.mode_off = p->total_modes;
         d.k_off = p->total_k;
         d.taup = (S.kind == MDX_KIND_TENSION) ? (float)S.tau : 0.f;
-        d.H_off = H_total;
         d.has_dir = (d.M > 0 && S.dH) ? 1 : 0;
-        any_dir = any_dir || d.has_dir;
-        if (d.M > 0) H_total += (long long)d.M * d.N * d.Npad;
         p->total_modes += d.N;
         p->total_k += d.M;
         p->dt[i] = S.dt;
@@ -282,7 +283,6 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
             gmd.push_back(S.gamma[m]);
             dtd.push_back(T);
         }
-        for (int k = 0; k < d.M; ++k) kap.push_back((float)S.kappa[k]);
         p->inst[i] = d;
     }
     const size_t TM = (size_t)p->total_modes;
@@ -303,43 +303,7 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
         if ((rc = upload(p, &p->d_omega2, w2d.data(), TM))) return bail(rc);
         if ((rc = upload(p, &p->d_gamma, gmd.data(), TM))) return bail(rc);
         if ((rc = upload(p, &p->d_dt, dtd.data(), TM))) return bail(rc);
-        if ((rc = upload(p, &p->d_kappa, kap.data(), kap.size()))) return bail(rc);
     }
-    // ---- coupling tensors: [M][N][Npad], rows zero padded
-    if (H_total > 0) {
-        int rc = dalloc(p, reinterpret_cast<void **>(&p->d_H), H_total * sizeof(float));
-        if (rc) return bail(rc);
-        if (any_dir) {
-            rc = dalloc(p, reinterpret_cast<void **>(&p->d_dH), H_total * sizeof(float));
-            if (rc) return bail(rc);
-            MDX_CUDA(cudaMemset(p->d_dH, 0, H_total * sizeof(float)), "memset dH");
-        }
-        std::vector<float> tmp;
-        for (int i = 0; i < n_inst; ++i) {
-            const InstDesc &d = p->inst[i];
-            if (d.M == 0) continue;
-            const size_t blk = (size_t)d.M * d.N * d.Npad;
-            for (int which = 0; which < (d.has_dir ? 2 : 1); ++which) {
-                const float *src = which == 0 ? I[i].H : I[i].dH;
-                tmp.assign(blk, 0.f);
-                for (int k = 0; k < d.M; ++k)
-                    for (int a = 0; a < d.N; ++a)
-                        std::memcpy(&tmp[((size_t)k * d.N + a) * d.Npad],
-                                    src + ((size_t)k * d.N + a) * d.N, d.N * sizeof(float));
-                float *dst = (which == 0 ? p->d_H : p->d_dH) + d.H_off;
-                MDX_CUDA(cudaMemcpy(dst, tmp.data(), blk * sizeof(float), cudaMemcpyHostToDevice),
-                         "upload H");
-            }
-        }
-    }
-    for (int i = 0; i < n_inst; ++i) {
-        InstDesc &d = p->inst[i];
-        d.dH_off = d.H_off;
-        // algorithmic bytes of one pass: the N x N block of every stress mode
-        p->H_bytes_per_step += 4.0 * d.M * d.N * d.N;
-        if (d.has_dir) p->dH_bytes_per_step += 4.0 * d.M * d.N * d.N;
-    }
-
     // ---- tension list (strings, membranes and plates without coupling)
     for (int i = 0; i < n_inst; ++i) {
         const InstDesc &d = p->inst[i];
@@ -360,6 +324,78 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
         MDX_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device), "attr");
         int max_cta = dev_sms;
         if (o.max_ctas > 0) max_cta = std::min(max_cta, o.max_ctas);
+        // Symmetry-class layout: used when every coupled plate gives classes
+        // that match its coupling tensor (entries outside the class pattern at
+        // most 1e-6 of the largest of their H^k; those are dropped).
+        bool parity = true;
+        for (int i = 0; i < n_inst; ++i) {
+            const InstDesc &d = p->inst[i];
+            if (d.kind == MDX_KIND_PLATE && d.M > 0 && (!I[i].phi_class || !I[i].psi_class))
+                parity = false;
+        }
+        std::vector<std::vector<int>> perm(n_inst), kperm(n_inst);
+        std::vector<std::vector<int>> kcls(n_inst);
+        for (int i = 0; i < n_inst; ++i) {
+            InstDesc &d = p->inst[i];
+            if (d.M == 0) continue;
+            kperm[i].resize(d.M);
+            std::iota(kperm[i].begin(), kperm[i].end(), 0);
+            if (!parity) continue;
+            const int *fc = I[i].phi_class, *kc = I[i].psi_class;
+            for (int m = 0; m < d.N; ++m)
+                if (fc[m] < 0 || fc[m] > 3)
+                    return bail(fail(MDX_ERR_ARG, "instance %d: phi_class[%d] outside 0..3", i, m));
+            for (int k = 0; k < d.M; ++k)
+                if (kc[k] < 0 || kc[k] > 3)
+                    return bail(fail(MDX_ERR_ARG, "instance %d: psi_class[%d] outside 0..3", i, k));
+            for (int which = 0; which < (d.has_dir ? 2 : 1); ++which) {
+                const float *src = which == 0 ? I[i].H : I[i].dH;
+                for (int k = 0; k < d.M; ++k) {
+                    const float *Hk = src + (size_t)k * d.N * d.N;
+                    float amax = 0.f;
+                    for (size_t t = 0; t < (size_t)d.N * d.N; ++t) amax = std::max(amax, std::fabs(Hk[t]));
+                    for (int x = 0; x < d.N; ++x)
+                        for (int y = 0; y < d.N; ++y)
+                            if ((fc[x] ^ fc[y]) != kc[k] &&
+                                std::fabs(Hk[(size_t)x * d.N + y]) > 1e-6f * amax)
+                                return bail(fail(MDX_ERR_ARG,
+                                    "instance %d: %s[%d][%d][%d] lies outside the declared symmetry classes",
+                                    i, which == 0 ? "H" : "dH", k, x, y));
+                }
+            }
+            d.parity = 1;
+            for (int a = 0; a < 4; ++a) d.ncls[a] = 0;
+            for (int m = 0; m < d.N; ++m) d.ncls[fc[m]]++;
+            d.ocls[0] = 0;
+            for (int a = 1; a < 4; ++a) d.ocls[a] = d.ocls[a - 1] + d.ncls[a - 1];
+            perm[i].resize(d.N);
+            int fill[4] = {d.ocls[0], d.ocls[1], d.ocls[2], d.ocls[3]};
+            for (int m = 0; m < d.N; ++m) perm[i][fill[fc[m]]++] = m;
+            std::stable_sort(kperm[i].begin(), kperm[i].end(),
+                             [&](int x, int y) { return kc[x] < kc[y]; });
+            kcls[i].resize(d.M);
+            for (int kk = 0; kk < d.M; ++kk) kcls[i][kk] = kc[kperm[i][kk]];
+        }
+        auto nb4 = [](int n) { return (n + 3) & ~3; };
+        // a class wider than 32 threads x kParQmax quads keeps the dense layout
+        for (int i = 0; i < n_inst && parity; ++i)
+            for (int a = 0; a < 4; ++a)
+                if (p->inst[i].M > 0 && nb4(p->inst[i].ncls[a]) / 4 > 32 * kParQmax) parity = false;
+        if (!parity)
+            for (int i = 0; i < n_inst; ++i) {
+                p->inst[i].parity = 0;
+                if (p->inst[i].M > 0) std::iota(kperm[i].begin(), kperm[i].end(), 0);
+            }
+        p->parity = parity;
+        // bytes (floats) one internal stress mode streams per pass
+        auto unit_cost = [&](int i, int kk) -> double {
+            const InstDesc &d = p->inst[i];
+            if (!parity) return (double)d.N * d.Npad;
+            const int c = kcls[i][kk];
+            double t = 0.0;
+            for (int a = 0; a < 4; ++a) t += (double)d.ncls[a] * nb4(d.ncls[a ^ c]);
+            return t;
+        };
         // Contiguous split: walk all (plate, stress mode) units in plan order
         // and cut the running H-byte count into G equal parts; each CTA then
         // holds at most one contiguous k range per plate.  A forced split
@@ -371,7 +407,7 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
         for (int i = 0; i < n_inst; ++i) {
             const InstDesc &d = p->inst[i];
             if (d.M == 0) continue;
-            total += (double)d.M * d.N * d.Npad;
+            for (int kk = 0; kk < d.M; ++kk) total += unit_cost(i, kk);
             total_kk += d.M;
         }
         const int G = (int)std::min<long long>(max_cta, total_kk);
@@ -383,8 +419,8 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
             for (int i = 0; i < n_inst; ++i) {
                 const InstDesc &d = p->inst[i];
                 if (d.M == 0) continue;
-                const double c = (double)d.N * d.Npad;
                 for (int k = 0; k < d.M; ++k) {
+                    const double c = unit_cost(i, k);
                     int g = (int)((cum + 0.5 * c) / target);
                     g = std::max(0, std::min(G - 1, g));
                     cum += c;
@@ -409,14 +445,17 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
             for (int i = 0; i < n_inst; ++i) {
                 const InstDesc &d = p->inst[i];
                 if (d.M == 0) continue;
-                const double cost = (double)d.M * d.N * d.Npad;
+                double cost = 0.0;
+                for (int kk = 0; kk < d.M; ++kk) cost += unit_cost(i, kk);
                 int np = (int)std::ceil(cost / target - 1e-9);
                 np = std::max(1, std::min(np, std::min(d.M, G)));
                 if (o.force_split > 0) np = std::max(np, std::min(o.force_split, std::min(d.M, G)));
                 for (int j = 0; j < np; ++j) {
                     const int k0 = (int)((long long)d.M * j / np);
                     const int k1 = (int)((long long)d.M * (j + 1) / np);
-                    pieces.push_back({i, k0, k1, (double)(k1 - k0) * d.N * d.Npad});
+                    double pc = 0.0;
+                    for (int kk = k0; kk < k1; ++kk) pc += unit_cost(i, kk);
+                    pieces.push_back({i, k0, k1, pc});
                 }
             }
             std::stable_sort(pieces.begin(), pieces.end(),
@@ -478,6 +517,151 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
         }
         p->n_cta = (int)cta_off.size() - 1;
         p->state_floats = max_state;
+        // ---- coupling data in HBM
+        // dense layout: per plate [M][N][N_pad] rows (zero padded);
+        // class layout: per item, per class chunk, super-blocks in stream order.
+        std::vector<ParityChunk> chunks;
+        long long H_total = 0;
+        int mc_glob = kParMcMax;
+        if (parity) {
+            for (int i = 0; i < n_inst; ++i) {
+                const InstDesc &d = p->inst[i];
+                if (d.M == 0) continue;
+                int nq = 1;
+                for (int a = 0; a < 4; ++a) nq = std::max(nq, nb4(d.ncls[a]) / 4);
+                const int cap = std::max(1, std::min(kParMcMax, 8192 / (2 * p->npad_max)));
+                int mc = cap;
+                auto tpk = [](int m) { int t = 32; while (t > 1 && t * m > 256) t >>= 1; return t; };
+                while (mc > 1 && tpk(mc) * kParQmax < nq) --mc;
+                mc_glob = std::min(mc_glob, mc);
+            }
+            for (auto &it : items) {
+                const InstDesc &d = p->inst[it.inst];
+                it.chunk0 = (int)chunks.size();
+                int kk = it.k0;
+                while (kk < it.k1) {
+                    const int c = kcls[it.inst][kk];
+                    int e = kk;
+                    while (e < it.k1 && kcls[it.inst][e] == c && e - kk < mc_glob) ++e;
+                    ParityChunk ch{};
+                    ch.c = c;
+                    ch.kl0 = kk;
+                    ch.mc = e - kk;
+                    long long sz = 0;
+                    for (int a = 0; a < 4; ++a) sz += (long long)d.ncls[a] * ch.mc * nb4(d.ncls[a ^ c]);
+                    ch.off = H_total;
+                    H_total += sz;
+                    ch.doff = d.has_dir ? H_total : 0;
+                    if (d.has_dir) H_total += sz;
+                    chunks.push_back(ch);
+                    kk = e;
+                }
+                it.chunk1 = (int)chunks.size();
+            }
+        } else {
+            for (int i = 0; i < n_inst; ++i) {
+                InstDesc &d = p->inst[i];
+                d.H_off = H_total;
+                if (d.M > 0) H_total += (long long)d.M * d.N * d.Npad;
+            }
+            for (int i = 0; i < n_inst; ++i) {
+                InstDesc &d = p->inst[i];
+                d.dH_off = H_total;
+                if (d.has_dir) H_total += (long long)d.M * d.N * d.Npad;
+            }
+        }
+        p->mc_max = mc_glob;
+        {
+            int rc2 = dalloc(p, reinterpret_cast<void **>(&p->d_H), std::max<long long>(H_total, 4) * sizeof(float));
+            if (rc2) return bail(rc2);
+            p->d_dH = p->d_H;
+            std::vector<float> tmp;
+            if (parity) {
+                for (const auto &it : items) {
+                    const InstDesc &d = p->inst[it.inst];
+                    for (int ci = it.chunk0; ci < it.chunk1; ++ci) {
+                        const ParityChunk &ch = chunks[ci];
+                        for (int which = 0; which < (d.has_dir ? 2 : 1); ++which) {
+                            const float *src = which == 0 ? I[it.inst].H : I[it.inst].dH;
+                            tmp.clear();
+                            for (int a = 0; a < 4; ++a) {
+                                const int bcl = a ^ ch.c, na = d.ncls[a], nbc = d.ncls[bcl];
+                                const int w = nb4(nbc);
+                                for (int pp = 0; pp < na; ++pp) {
+                                    const int row = perm[it.inst][d.ocls[a] + pp];
+                                    for (int kl = 0; kl < ch.mc; ++kl) {
+                                        const int ku = kperm[it.inst][ch.kl0 + kl];
+                                        const float *Hr = src + ((size_t)ku * d.N + row) * d.N;
+                                        for (int cs = 0; cs < w; ++cs)
+                                            tmp.push_back(cs < nbc ? Hr[perm[it.inst][d.ocls[bcl] + cs]] : 0.f);
+                                    }
+                                }
+                            }
+                            float *dst = p->d_H + (which == 0 ? ch.off : ch.doff);
+                            if (!tmp.empty())
+                                MDX_CUDA(cudaMemcpy(dst, tmp.data(), tmp.size() * sizeof(float),
+                                                    cudaMemcpyHostToDevice), "upload H");
+                        }
+                    }
+                }
+            } else {
+                for (int i = 0; i < n_inst; ++i) {
+                    const InstDesc &d = p->inst[i];
+                    if (d.M == 0) continue;
+                    const size_t blk = (size_t)d.M * d.N * d.Npad;
+                    for (int which = 0; which < (d.has_dir ? 2 : 1); ++which) {
+                        const float *src = which == 0 ? I[i].H : I[i].dH;
+                        tmp.assign(blk, 0.f);
+                        for (int k = 0; k < d.M; ++k)
+                            for (int a2 = 0; a2 < d.N; ++a2)
+                                std::memcpy(&tmp[((size_t)k * d.N + a2) * d.Npad],
+                                            src + ((size_t)k * d.N + a2) * d.N, d.N * sizeof(float));
+                        float *dst = p->d_H + (which == 0 ? d.H_off : d.dH_off);
+                        MDX_CUDA(cudaMemcpy(dst, tmp.data(), blk * sizeof(float), cudaMemcpyHostToDevice),
+                                 "upload H");
+                    }
+                }
+            }
+            // algorithmic bytes of one pass (the stored, structurally nonzero part of H)
+            for (int i = 0; i < n_inst; ++i) {
+                const InstDesc &d = p->inst[i];
+                if (d.M == 0) continue;
+                double per_step = 0.0;
+                if (parity) {
+                    for (int kk = 0; kk < d.M; ++kk) {
+                        const int c = kcls[i][kk];
+                        for (int a = 0; a < 4; ++a) per_step += 4.0 * d.ncls[a] * d.ncls[a ^ c];
+                    }
+                } else {
+                    per_step = 4.0 * d.M * d.N * d.N;
+                }
+                p->H_bytes_per_step += per_step;
+                if (d.has_dir) p->dH_bytes_per_step += per_step;
+            }
+            // kappa in internal (class-sorted) order, class permutations
+            std::vector<float> kap2;
+            std::vector<int> perm_all, kperm_all;
+            for (int i = 0; i < n_inst; ++i) {
+                InstDesc &d = p->inst[i];
+                for (int kk = 0; kk < d.M; ++kk) kap2.push_back((float)I[i].kappa[kperm[i][kk]]);
+                d.perm_off = (long long)perm_all.size();
+                for (int v : perm[i]) perm_all.push_back(v);
+                for (int kk = 0; kk < d.M; ++kk) kperm_all.push_back(kperm[i][kk]);
+            }
+            if ((rc2 = upload(p, &p->d_kappa, kap2.data(), kap2.size()))) return bail(rc2);
+            if ((rc2 = upload(p, &p->d_perm, perm_all.data(), perm_all.size()))) return bail(rc2);
+            if ((rc2 = upload(p, &p->d_kperm, kperm_all.data(), kperm_all.size()))) return bail(rc2);
+            if ((rc2 = upload(p, &p->d_chunks, chunks.data(), chunks.size()))) return bail(rc2);
+        }
+        p->min_stage_floats = p->npad_max;
+        if (parity) {
+            for (const auto &it : items) {
+                const InstDesc &d = p->inst[it.inst];
+                for (int ci = it.chunk0; ci < it.chunk1; ++ci)
+                    for (int a = 0; a < 4; ++a)
+                        p->min_stage_floats = std::max(p->min_stage_floats, chunks[ci].mc * nb4(d.ncls[a]));
+            }
+        }
         // ring: stages of >= one padded row, filling the remaining shared memory
         p->smem_optin = smem_optin;
         {
@@ -514,28 +698,34 @@ namespace {
 // allows, separately for the forward and the reverse launch.
 int configure_tiles(mdx_plan *p, int stage_req, int ring_req) {
     const int smem_optin = p->smem_optin;
+    const int min_stage = std::max(p->min_stage_floats, p->npad_max) * 4;
     int stage = stage_req > 0 ? stage_req : 64 * 1024;
-    stage = std::max(stage, p->npad_max * 4);
+    stage = std::max(stage, min_stage);
     stage = (stage + 15) & ~15;
-    if (stage_req <= 0) {
-        while (stage > 16 * 1024 && stage / 2 >= p->npad_max * 4 &&
-               plate_smem_bytes(2, stage, 3, p->state_floats) + 1024 > (size_t)smem_optin)
-            stage = ((stage / 2) + 15) & ~15;
-    }
     bool dir = false;
     for (const auto &d : p->inst) dir = dir || d.has_dir;
     const int us_fwd = 1, us_rev = dir ? 3 : 2;
+    auto ufl = [&](int us) {
+        // partial sums: dense row groups [kChunkK][slots][1024]; class chunks
+        // [mc][u, z][N_pad] (the direction pass needs no stored vector)
+        return p->parity ? p->mc_max * 2 * p->npad_max : kChunkK * us * kUPartFloats;
+    };
+    if (stage_req <= 0) {
+        while (stage > 16 * 1024 && stage / 2 >= min_stage &&
+               plate_smem_bytes(2, stage, ufl(us_rev), p->state_floats) + 1024 > (size_t)smem_optin)
+            stage = ((stage / 2) + 15) & ~15;
+    }
     int ring_f = 0, ring_r = 0;
     size_t smem_f = 0, smem_r = 0;
     for (int which = 0; which < 2; ++which) {
         const int us = which == 0 ? us_fwd : us_rev;
-        const size_t fixed = plate_smem_bytes(0, stage, us, p->state_floats);
+        const size_t fixed = plate_smem_bytes(0, stage, ufl(us), p->state_floats);
         if (fixed + 2 * (size_t)stage + 1024 > (size_t)smem_optin)
             return fail(MDX_ERR_UNSUPPORTED, "plate kernel needs %zu B of shared memory (> %d)",
                         fixed + 2 * (size_t)stage, smem_optin);
         int ring = ring_req > 0 ? ring_req : (int)((size_t)(smem_optin - 1024 - fixed) / stage);
         ring = std::max(2, std::min(ring, 16));
-        const size_t need = plate_smem_bytes(ring, stage, us, p->state_floats);
+        const size_t need = plate_smem_bytes(ring, stage, ufl(us), p->state_floats);
         if (need > (size_t)smem_optin)
             return fail(MDX_ERR_UNSUPPORTED, "plate kernel needs %zu B of shared memory (> %d)",
                         need, smem_optin);
@@ -546,6 +736,8 @@ int configure_tiles(mdx_plan *p, int stage_req, int ring_req) {
     p->stage_bytes = stage;
     p->u_slots_fwd = us_fwd;
     p->u_slots_rev = us_rev;
+    p->u_floats_fwd = ufl(us_fwd);
+    p->u_floats_rev = ufl(us_rev);
     p->ring_fwd = ring_f;
     p->ring_rev = ring_r;
     p->smem_fwd = smem_f;
@@ -570,6 +762,11 @@ PlateParams base_plate(mdx_plan *p, int mode, int steps, int n_begin, int total_
     P.stage_bytes = p->stage_bytes;
     P.ring_stages = (mode == MODE_REVERSE) ? p->ring_rev : p->ring_fwd;
     P.u_slots = (mode == MODE_REVERSE) ? p->u_slots_rev : p->u_slots_fwd;
+    P.u_floats = (mode == MODE_REVERSE) ? p->u_floats_rev : p->u_floats_fwd;
+    P.parity = p->parity ? 1 : 0;
+    P.npad_max = p->npad_max;
+    P.chunks = p->d_chunks;
+    P.perm = p->d_perm;
     P.max_spt = (p->npad_max + kPlateThreads - 1) / kPlateThreads;
     P.smem_state_floats = p->state_floats;
     P.total_modes = p->total_modes;
@@ -729,6 +926,7 @@ extern "C" int mdx_grad(mdx_plan *p, const float *exc, const double *q0, const d
         P.mode = T.mode = MODE_REVERSE;
         P.ring_stages = p->ring_rev;
         P.u_slots = p->u_slots_rev;
+        P.u_floats = p->u_floats_rev;
         P.ybar = T.ybar = d_audio;
         P.adj = T.adj = w.adj;
         P.gacc = T.gacc = w.gacc;
@@ -751,6 +949,7 @@ extern "C" int mdx_grad(mdx_plan *p, const float *exc, const double *q0, const d
     g.kacc = w.kacc;
     g.diracc = w.diracc;
     g.tacc = w.tacc;
+    g.kperm = p->d_kperm;
     if (out) {
         g.d_omega2 = out->d_omega2;
         g.d_gamma = out->d_gamma;

@@ -114,8 +114,32 @@ struct Smem {
 
 }  // namespace
 
+// Threads per stress mode in the class layout: the largest power of two
+// <= 32 with mc * tpk <= 256.
+__host__ __device__ __forceinline__ int par_tpk(int mc) {
+    int t = 32;
+    while (t > 1 && t * mc > kPlateThreads) t >>= 1;
+    return t;
+}
+
+// Element of a 4-array by a run-time index without forcing the array into
+// local memory (selects only).
+__device__ __forceinline__ int pick4(const int (&v)[4], int a) {
+    return a == 0 ? v[0] : (a == 1 ? v[1] : (a == 2 ? v[2] : v[3]));
+}
+__device__ __forceinline__ float comp4(const float4 &v, int e) {
+    return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ void fma4(float4 &acc, const float4 &h, float x) {
+    acc.x = fmaf(h.x, x, acc.x);
+    acc.y = fmaf(h.y, x, acc.y);
+    acc.z = fmaf(h.z, x, acc.z);
+    acc.w = fmaf(h.w, x, acc.w);
+}
+
 // R: right-hand sides of the H pass (1: forward / recompute; 2: reverse).
-template <int R>
+// PAR: coupling stored in symmetry-class chunks (see ParityChunk).
+template <int R, bool PAR>
 __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams P) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int tid = threadIdx.x;
@@ -136,7 +160,7 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
     S.ring = reinterpret_cast<float *>(p);
     p += (size_t)RING * P.stage_bytes;
     S.U = reinterpret_cast<float *>(p);
-    p += (size_t)kChunkK * P.u_slots * kUPartFloats * sizeof(float);
+    p += (size_t)P.u_floats * sizeof(float);
     S.red = reinterpret_cast<float *>(p);
     p += (size_t)2 * kChunkK * 4 * kPlateWarps * sizeof(float);
     S.red2 = reinterpret_cast<float *>(p);
@@ -168,6 +192,37 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                     const InstDesc d = P.inst[item.inst];
                     const int rows_per_stage = max(1, stage_floats / d.Npad);
                     const int nmat = (reverse && d.has_dir) ? 2 : 1;
+                    if constexpr (PAR) {
+                        // class chunks: super-blocks a = 0..3, rows of mc * nb4 floats
+                        for (int ci = item.chunk0; ci < item.chunk1 && ok; ++ci) {
+                            const ParityChunk ch = P.chunks[ci];
+                            for (int mat = 0; mat < nmat && ok; ++mat) {
+                                const float *base = P.H + (mat == 0 ? ch.off : ch.doff);
+                                long long cur = 0;
+                                for (int a = 0; a < 4 && ok; ++a) {
+                                    const int na = pick4(d.ncls, a), nbc = pick4(d.ncls, a ^ ch.c);
+                                    if (na == 0 || nbc == 0) continue;
+                                    const int L = ch.mc * ((nbc + 3) & ~3);
+                                    const int rps = max(1, stage_floats / L);
+                                    for (int p0 = 0; p0 < na; p0 += rps) {
+                                        const int nr = min(rps, na - p0);
+                                        const int s = (int)(seq % RING);
+                                        const uint32_t ph = (uint32_t)((seq / RING) & 1);
+                                        if (!mbar_wait(&S.empty[s], ph ^ 1u, P.wait_limit, gabort)) {
+                                            ok = false;
+                                            break;
+                                        }
+                                        const uint32_t bytes = (uint32_t)nr * L * 4u;
+                                        mbar_arrive_expect_tx(&S.full[s], bytes);
+                                        bulk_g2s(S.ring + (size_t)s * stage_floats, base + cur, bytes,
+                                                 &S.full[s]);
+                                        cur += (long long)nr * L;
+                                        ++seq;
+                                    }
+                                }
+                            }
+                        }
+                    } else {
                     for (int k = item.k0; k < item.k1 && ok; ++k) {
                         for (int mat = 0; mat < nmat && ok; ++mat) {
                             const float *base = (mat == 0 ? P.H + d.H_off : P.dH + d.dH_off) +
@@ -187,6 +242,7 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                                 ++seq;
                             }
                         }
+                    }
                     }
                 }
             }
@@ -275,6 +331,22 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
             }
         }
         consumer_bar();
+        if constexpr (PAR) {
+            // right-hand sides in class order
+            for (int ii = it0; ii < it1; ++ii) {
+                const PlateItem item = P.items[ii];
+                const InstDesc d = P.inst[item.inst];
+                float *st = S.state + item.smem_state;
+                const int Np = d.Npad;
+                const float *q = reverse ? st + ST_SRC0 * Np : st + ST_QHI * Np;
+                for (int mp = tid; mp < d.N; mp += kPlateThreads) {
+                    const int su = P.perm[d.perm_off + mp];
+                    st[ST_QP * Np + mp] = q[su];
+                    if (reverse) st[ST_WP * Np + mp] = st[ST_SRC1 * Np + su];
+                }
+            }
+            consumer_bar();
+        }
 
         // -------- phase A: coupling pass over this CTA's items
         // Thread layout over a stage of rows (p) x columns (s) of H^k: thread
@@ -295,6 +367,149 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
             const float *src0 = reverse ? st + ST_SRC0 * Np : st + ST_QHI * Np;
             const float *src1 = st + ST_SRC1 * Np;
             const int spt = (Np + kPlateThreads - 1) / kPlateThreads;
+            if constexpr (PAR) {
+                const float *qp = st + ST_QP * Np;
+                const float *wp = st + ST_WP * Np;
+                float *red = S.red;
+                for (int ci = item.chunk0; ci < item.chunk1; ++ci) {
+                    const ParityChunk ch = P.chunks[ci];
+                    const int mc = ch.mc;
+                    const int tpk = par_tpk(mc);
+                    const int kl = tid / tpk, c4 = tid - (tid / tpk) * tpk;
+                    const bool kact = kl < mc;
+                    float dsum[4] = {0.f, 0.f, 0.f, 0.f};
+                    for (int mat = 0; mat < nmat; ++mat) {
+                        for (int a = 0; a < 4; ++a) {
+                            const int bcl = a ^ ch.c;
+                            const int na = pick4(d.ncls, a), nbc = pick4(d.ncls, bcl);
+                            if (na == 0 || nbc == 0) continue;
+                            const int oa = pick4(d.ocls, a), ob = pick4(d.ocls, bcl);
+                            const int nb4 = (nbc + 3) & ~3, nq = nb4 >> 2;
+                            const int L = mc * nb4;
+                            const int rps = max(1, stage_floats / L);
+                            // each thread owns column quads qi0 = c4 and qi1 = c4 + tpk
+                            const int qi0 = c4, qi1 = c4 + tpk;
+                            const bool h0 = kact && qi0 < nq, h1 = kact && qi1 < nq;
+                            const bool two = (R > 1) && (mat == 0);
+                            float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
+                            for (int p0 = 0; p0 < na; p0 += rps) {
+                                const int nr = min(rps, na - p0);
+                                const int s = (int)(seq % RING);
+                                const uint32_t ph = (uint32_t)((seq / RING) & 1);
+                                if (!fail && !mbar_wait(&S.full[s], ph, P.wait_limit, gabort)) {
+                                    fail = true;
+                                    *reinterpret_cast<volatile int *>(&S.misc[1]) = 1;
+                                    atomicExch((int *)gabort, 1);
+                                }
+                                if (h0) {
+                                    const float *row = S.ring + (size_t)s * stage_floats + kl * nb4 + 4 * qi0;
+                                    const float *xs = qp + oa + p0;
+                                    const float *ys = wp + oa + p0;
+                                    if (h1) {
+#pragma unroll 2
+                                        for (int r = 0; r < nr; ++r) {
+                                            const float4 hA = *reinterpret_cast<const float4 *>(row + (size_t)r * L);
+                                            const float4 hB = *reinterpret_cast<const float4 *>(row + (size_t)r * L + 4 * tpk);
+                                            const float x = xs[r];
+                                            fma4(a0, hA, x);
+                                            fma4(b0, hB, x);
+                                            if (two) {
+                                                const float y = ys[r];
+                                                fma4(a1, hA, y);
+                                                fma4(b1, hB, y);
+                                            }
+                                        }
+                                    } else {
+#pragma unroll 4
+                                        for (int r = 0; r < nr; ++r) {
+                                            const float4 hA = *reinterpret_cast<const float4 *>(row + (size_t)r * L);
+                                            fma4(a0, hA, xs[r]);
+                                            if (two) fma4(a1, hA, ys[r]);
+                                        }
+                                    }
+                                }
+                                __syncwarp();
+                                if (lane == 0) mbar_arrive(&S.empty[s]);
+                                ++seq;
+                            }
+                            // this super-block completes u^k (and z^k, t^k) on the columns of class b
+#pragma unroll
+                            for (int half = 0; half < 2; ++half) {
+                                const bool has = half == 0 ? h0 : h1;
+                                if (!has) continue;
+                                const int qi = half == 0 ? qi0 : qi1;
+                                const float4 va = half == 0 ? a0 : b0;
+                                const float4 vb = half == 0 ? a1 : b1;
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) {
+                                    const int cs = 4 * qi + e;
+                                    if (cs >= nbc) break;
+                                    const int mp = ob + cs;
+                                    const float v0 = comp4(va, e);
+                                    if (mat == 0) {
+                                        S.U[((size_t)kl * 2 + 0) * P.npad_max + mp] = v0;
+                                        dsum[0] = fmaf(qp[mp], v0, dsum[0]);
+                                        if (R > 1) {
+                                            S.U[((size_t)kl * 2 + 1) * P.npad_max + mp] = comp4(vb, e);
+                                            dsum[1] = fmaf(wp[mp], v0, dsum[1]);
+                                        }
+                                    } else {
+                                        dsum[2] = fmaf(qp[mp], v0, dsum[2]);
+                                        dsum[3] = fmaf(wp[mp], v0, dsum[3]);
+                                    }
+                                }
+                            }
+                        }
+                    }
+                    // dot products of each stress mode: reduce over its tpk lanes
+#pragma unroll
+                    for (int dd = 0; dd < 4; ++dd) {
+                        float v = dsum[dd];
+                        for (int o = tpk >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                        if (kact && c4 == 0) red[kl * 4 + dd] = v;
+                    }
+                    consumer_bar();
+                    // forces, per mode in class order (each thread owns distinct modes)
+                    for (int mp = tid; mp < d.N; mp += kPlateThreads) {
+                        const int su = P.perm[d.perm_off + mp];
+                        float fa = 0.f, fb = 0.f;
+                        for (int q = 0; q < mc; ++q) {
+                            const float kap = P.kappa[d.k_off + ch.kl0 + q];
+                            const float eta = red[q * 4 + 0];
+                            const float u = S.U[((size_t)q * 2 + 0) * P.npad_max + mp];
+                            if (!reverse) {
+                                fa = fmaf(kap * eta, u, fa);
+                            } else {
+                                const float z = S.U[((size_t)q * 2 + 1) * P.npad_max + mp];
+                                fb = fmaf(kap * eta, u, fb);
+                                fa = fmaf(kap, fmaf(2.f * red[q * 4 + 1], u, eta * z), fa);
+                            }
+                        }
+                        st[ST_FLOC * Np + su] += fa;
+                        if (reverse) st[ST_FLOC2 * Np + su] += fb;
+                    }
+                    if (reverse && tid == 0) {
+                        for (int q = 0; q < mc; ++q) {
+                            const long long kk = d.k_off + ch.kl0 + q;
+                            const float kap = P.kappa[kk];
+                            const float eta = red[q * 4 + 0], xi = red[q * 4 + 1];
+                            float *ka = P.kacc + 2 * kk;
+                            float s0 = ka[0], c0 = ka[1];
+                            kahan_add(s0, c0, -eta * xi);
+                            ka[0] = s0;
+                            ka[1] = c0;
+                            if (d.has_dir) {
+                                float *da = P.diracc + 2 * kk;
+                                float s1 = da[0], c1 = da[1];
+                                kahan_add(s1, c1, -kap * fmaf(xi, red[q * 4 + 2], eta * red[q * 4 + 3]));
+                                da[0] = s1;
+                                da[1] = c1;
+                            }
+                        }
+                    }
+                    consumer_bar();
+                }
+            } else {
             for (int kc = item.k0; kc < item.k1; kc += kChunkK) {
                 const int nk = min(kChunkK, item.k1 - kc);
                 float *red = S.red + chunk_parity * (kChunkK * 4 * kPlateWarps);
@@ -449,6 +664,7 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                     }
                 }
                 chunk_parity ^= 1;
+            }
             }
             // publish partial forces of a shared plate
             if (d.n_contrib > 1) {
@@ -621,11 +837,11 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
     }
 }
 
-size_t plate_smem_bytes(int ring_stages, int stage_bytes, int u_slots, int state_floats) {
+size_t plate_smem_bytes(int ring_stages, int stage_bytes, int u_floats, int state_floats) {
     size_t b = 2 * ring_stages * sizeof(uint64_t) + 16 * sizeof(int);
     b = (b + 127) & ~size_t(127);
     b += (size_t)ring_stages * stage_bytes;
-    b += (size_t)kChunkK * u_slots * kUPartFloats * sizeof(float);
+    b += (size_t)u_floats * sizeof(float);
     b += (size_t)2 * kChunkK * 4 * kPlateWarps * sizeof(float);
     b += (size_t)2 * 2 * kPlateWarps * sizeof(float);
     b += (size_t)state_floats * sizeof(float);
@@ -633,11 +849,12 @@ size_t plate_smem_bytes(int ring_stages, int stage_bytes, int u_slots, int state
 }
 
 cudaError_t plate_set_smem_limit(size_t smem) {
-    cudaError_t e = cudaFuncSetAttribute(plate_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(plate_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem);
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(plate_kernel<1, false>, A, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(plate_kernel<2, false>, A, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(plate_kernel<1, true>, A, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(plate_kernel<2, true>, A, (int)smem);
+    return e;
 }
 
 // Cooperative launch (all CTAs resident: the per-plate exchange waits on
@@ -655,8 +872,12 @@ cudaError_t launch_plate(const PlateParams &p, int grid, size_t smem, cudaStream
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (p.mode == MODE_REVERSE) return cudaLaunchKernelEx(&cfg, plate_kernel<2>, p);
-    return cudaLaunchKernelEx(&cfg, plate_kernel<1>, p);
+    if (p.parity) {
+        if (p.mode == MODE_REVERSE) return cudaLaunchKernelEx(&cfg, plate_kernel<2, true>, p);
+        return cudaLaunchKernelEx(&cfg, plate_kernel<1, true>, p);
+    }
+    if (p.mode == MODE_REVERSE) return cudaLaunchKernelEx(&cfg, plate_kernel<2, false>, p);
+    return cudaLaunchKernelEx(&cfg, plate_kernel<1, false>, p);
 }
 
 }  // namespace mdx

@@ -122,15 +122,22 @@ def prepare(inst, fs, steps, coupling="auto", want_aspect_derivative=False):
         M = inst.n_psi if n_eff >= inst.n_phi else min(inst.n_psi, max(1, inst.n_psi * n_eff // inst.n_phi))
         out["tau"] = 0.0
         if inst.nonlinear and M > 0 and coupling is not None:
+            psi_cls = None
             if callable(coupling):
                 H, zeta4 = coupling(inst, labels, M)
                 dH = dz = None
             elif want_aspect_derivative:
-                H, zeta4, dH, dz = _coupling.coupling_with_aspect_derivative(
+                H, zeta4, dH, dz, psi_cls = _coupling.coupling_with_aspect_derivative(
                     inst.area, inst.aspect, labels, M)
             else:
-                H, zeta4 = _coupling.coupling_tensor(Lx, Ly, labels, M)
+                airy = _coupling.airy_modes(Lx, Ly, M)
+                H, zeta4 = _coupling.coupling_tensor(Lx, Ly, labels, M, airy=airy)
+                psi_cls = _coupling.airy_classes(airy[1])
                 dH = dz = None
+            if psi_cls is not None:
+                # symmetry classes: H^k_ij vanishes unless class(i) ^ class(j) == class(k)
+                out["phi_class"] = _coupling.transverse_classes(labels)
+                out["psi_class"] = psi_cls
             out["H"] = H.astype(np.float32)
             out["zeta4"] = zeta4
             out["kappa"] = inst.E / (2.0 * inst.rho_vol * zeta4)

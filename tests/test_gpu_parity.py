@@ -40,18 +40,32 @@ def oracle_instance(inst, fs, steps, coupling=True):
     return oi
 
 
-def to_plan(oi, fs):
+def classes_of(oi):
+    """Symmetry classes of the oracle's modes: transverse from (m, n), Airy
+    from the position of the largest entry of each H^k."""
+    m, n = oi.labels[:, 0], oi.labels[:, 1]
+    fc = (2 * ((m + 1) % 2) + ((n + 1) % 2)).astype(np.int32)
+    kc = []
+    for Hk in oi.H:
+        i, j = np.unravel_index(np.argmax(np.abs(Hk)), Hk.shape)
+        kc.append(fc[i] ^ fc[j])
+    return fc, np.array(kc, dtype=np.int32)
+
+
+def to_plan(oi, fs, layout="classes"):
     d = dict(kind="plate" if oi.kind == "plate" else "tension", omega2=oi.omega2,
              gamma=oi.gamma, b=oi.b, c=oi.c, dt=1.0 / fs, lam=oi.lam, tau=oi.taup,
              e=oi.e, q0=oi.q0, qm1=oi.qm1)
     if oi.kind == "plate" and oi.H is not None:
         d["H"] = oi.H.astype(np.float32)
         d["kappa"] = oi.kappa
+        if layout == "classes":
+            d["phi_class"], d["psi_class"] = classes_of(oi)
     return d
 
 
-def run_gpu(ois, fs, steps, **opts):
-    sim = modal.Simulator([to_plan(o, fs) for o in ois], **opts)
+def run_gpu(ois, fs, steps, layout="classes", **opts):
+    sim = modal.Simulator([to_plan(o, fs, layout) for o in ois], **opts)
     r = sim.simulate(steps, want_state=True, want_status=True)
     torch.cuda.synchronize()
     off = sim.plan.mode_offset
@@ -60,8 +74,8 @@ def run_gpu(ois, fs, steps, **opts):
             r["status"].cpu().numpy(), sim)
 
 
-def check_parity(ois, fs, steps, tol=TOL, **opts):
-    audio, qend, status, _ = run_gpu(ois, fs, steps, **opts)
+def check_parity(ois, fs, steps, tol=TOL, layout="classes", **opts):
+    audio, qend, status, _ = run_gpu(ois, fs, steps, layout, **opts)
     assert (status == 0).all(), status
     for i, oi in enumerate(ois):
         ref = oracle.forward(oi, steps=steps)
@@ -88,11 +102,25 @@ def test_string_sizes(n):
     check_parity([oracle_instance(wl.instances[0], wl.fs, wl.steps)], wl.fs, wl.steps)
 
 
+@pytest.mark.parametrize("layout", ["dense", "classes"])
 @pytest.mark.parametrize("n,m", [(4, 1), (31, 3), (33, 8), (64, 16), (257, 9)])
-def test_plate_sizes(n, m):
+def test_plate_sizes(n, m, layout):
     wl = W.tiny_random(7 + n, "plate", n, m, steps=1200)
     wl.instances[0].F0 = 200.0
-    check_parity([oracle_instance(wl.instances[0], wl.fs, wl.steps)], wl.fs, wl.steps)
+    check_parity([oracle_instance(wl.instances[0], wl.fs, wl.steps)], wl.fs, wl.steps,
+                 layout=layout)
+
+
+def test_class_layout_equals_dense_layout():
+    """Streaming only the nonzero symmetry-class blocks gives the dense
+    layout's results up to FP32 summation order."""
+    wl = W.tiny_random(77, "plate", 120, 30, steps=2000)
+    wl.instances[0].F0 = 300.0
+    oi = oracle_instance(wl.instances[0], wl.fs, wl.steps)
+    a, qa, _, _ = run_gpu([oi], wl.fs, wl.steps, layout="dense")
+    b, qb, _, sim = run_gpu([oi], wl.fs, wl.steps, layout="classes", force_split=3)
+    assert sim.plan.tiles()["ctas"] >= 3
+    assert rel(b, a) <= 1e-6 and rel(qb[0], qa[0]) <= 1e-6
 
 
 def test_plate_split_over_ctas_matches_single_and_oracle():
@@ -142,18 +170,25 @@ def _grad_case(kind, seed, steps):
     return oi, wl.fs
 
 
-@pytest.mark.parametrize("kind", ["string", "plate"])
+@pytest.mark.parametrize("kind", ["string", "plate-dense", "plate-classes"])
 def test_gradients_match_oracle_adjoint(kind):
     steps = 1500
+    layout = kind.split("-")[1] if "-" in kind else "dense"
+    kind = kind.split("-")[0]
     oi, fs = _grad_case(kind, 31, steps)
     rng = np.random.default_rng(1)
     ybar = rng.normal(size=steps)
     # direction tensor for <dL/dH, dH>: a fixed symmetric random tensor
+    # (restricted to the symmetry-class pattern for the class layout)
     dH = None
-    d = to_plan(oi, fs)
+    d = to_plan(oi, fs, layout)
     if kind == "plate":
         R = rng.normal(size=oi.H.shape)
-        dH = (R + R.transpose(0, 2, 1)).astype(np.float32)
+        dH = (R + R.transpose(0, 2, 1))
+        if layout == "classes":
+            fc, kc = classes_of(oi)
+            dH = dH * ((fc[:, None] ^ fc[None, :])[None] == kc[:, None, None])
+        dH = dH.astype(np.float32)
         d["dH"] = dH
     sim = modal.Simulator([d])
     K = 256

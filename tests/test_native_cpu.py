@@ -121,7 +121,7 @@ def test_product_coupling_matches_oracle():
 def test_aspect_derivative_matches_secant():
     inst = W.tiny_random(6, "plate", 20, 5).instances[0]
     labels, _ = PO.rect_modes(inst, 20)
-    H, z, dH, dz = PC.coupling_with_aspect_derivative(inst.area, inst.aspect, labels, 5)
+    H, z, dH, dz, _ = PC.coupling_with_aspect_derivative(inst.area, inst.aspect, labels, 5)
     h = 1e-3 * inst.aspect
     Hp, zp = PC.coupling_tensor(*PC.sides(inst.area, inst.aspect + h), labels, 5)
     Hm, zm = PC.coupling_tensor(*PC.sides(inst.area, inst.aspect - h), labels, 5)
@@ -131,3 +131,22 @@ def test_aspect_derivative_matches_secant():
     sec = (sp * Hp - sm * Hm) / (2 * h)
     assert np.abs(dH - sec).max() <= 1e-4 * np.abs(sec).max()
     np.testing.assert_allclose(dz, (zp - zm) / (2 * h), rtol=1e-5)
+
+
+def test_coupling_symmetry_classes():
+    """H^k_ij vanishes (to rounding) unless class(i) ^ class(j) == class(k);
+    a quarter of the tensor is structurally nonzero."""
+    inst = W.tiny_random(7, "plate", 120, 30).instances[0]
+    labels, _ = PO.rect_modes(inst, 120)
+    Lx, Ly = PO.rect_sides(inst)
+    airy = PC.airy_modes(Lx, Ly, 30)
+    H, _ = PC.coupling_tensor(Lx, Ly, labels, 30, airy=airy)
+    fc = PC.transverse_classes(labels)
+    kc = PC.airy_classes(airy[1])
+    mask = (fc[:, None] ^ fc[None, :])[None] == kc[:, None, None]
+    assert np.abs(H[~mask]).max() <= 1e-12 * np.abs(H).max()
+    assert 0.2 < mask.mean() < 0.3
+    # the same classes describe the oracle's independently generated tensor (its
+    # full-basis eigensolver mixes the parity blocks at solver rounding, ~1e-10)
+    Ho, _ = CO.coupling_H(inst, labels, 30)
+    assert np.abs(Ho[~mask]).max() <= 1e-9 * np.abs(Ho).max()
