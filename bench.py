@@ -271,6 +271,7 @@ def main():
     value = units / (ms_step * 1e-3)
     # roofline of the dominant kernel (plate kernel: forward, recompute, reverse launches)
     stats = {w: sim.plan.kernel_stats(w) for w in (0, 1, 2)}
+    dir_stats = sim.plan.kernel_stats(3)
     sim.plan.set_profiling(False)
     peak, peak_kind = load_peaks()
     tot_ms = sum(s[1] for s in stats.values())
@@ -285,6 +286,7 @@ def main():
                 "kernel_share_of_step": tot_ms / ms_total if ms_total else None,
                 "per_launch_ms": d_ms / max(n_l, 1),
                 "per_launch_algorithmic_bytes": d_bytes / max(n_l, 1)}
+    roofline["direction_contraction"] = {"launches": dir_stats[0], "ms": dir_stats[1]}
     roofline["all_plate_kernels"] = {
         names[w]: {"launches": s[0], "ms": s[1],
                    "GB/s": (s[2] / (s[1] * 1e-3) / 1e9) if s[1] else None}

@@ -215,7 +215,8 @@ int mdx_plan_tiles(const mdx_plan *plan, int *stage_bytes, int *ring_fwd, int *r
  * Kernel timing (tracing).  When enabled, every plate-kernel launch of the
  * plan is bracketed by CUDA events on its launch stream.  mdx_plan_kernel_stats
  * synchronises those events and returns, for one launch class
- * (0 = forward, 1 = checkpoint recompute, 2 = reverse sweep), the number of
+ * (0 = forward, 1 = checkpoint recompute, 2 = reverse sweep, 3 = per-segment
+ * contraction of the direction tensor), the number of
  * launches, their summed device time in ms and their summed algorithmic bytes
  * (coupling-tensor bytes each launch must stream: one pass over H per step,
  * plus one over dH per reverse step when a direction tensor is planned).

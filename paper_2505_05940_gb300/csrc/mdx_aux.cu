@@ -102,7 +102,8 @@ __global__ void grad_epilogue_kernel(const GradEpilogue g) {
         double dir = 0.0;
         for (int k = 0; k < d.M; ++k) {
             if (g.d_kappa) g.d_kappa[d.k_off + g.kperm[d.k_off + k]] = kval(g.kacc + 2 * (d.k_off + k));
-            if (d.has_dir) dir += kval(g.diracc + 2 * (d.k_off + k));
+            if (d.has_dir)
+                for (int a = 0; a < 4; ++a) dir += g.dir_acc[(d.k_off + k) * 4 + a];
         }
         if (g.d_dir) g.d_dir[i] = dir;
     }

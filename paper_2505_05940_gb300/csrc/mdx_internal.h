@@ -150,7 +150,9 @@ struct PlateParams {
     float *adj;                   // [AD_N][total_modes]
     float *gacc;                  // [GA_N][2][total_modes]
     float *kacc;                  // [total stress modes][2] d kappa (Kahan pair)
-    float *diracc;                // [total stress modes][2] directional derivative per k (Kahan pair)
+    float *seg_w;                 // reverse: [steps][total_modes] w^n = r a^{n+1} (owners)
+    float *xe;                    // reverse: [steps][2][total_k] xi_k^n, eta_k^n
+    long long total_k;
     // synchronisation
     float *part;                  // exchange slots, two parities of part_stride floats
     long long part_stride;
@@ -159,6 +161,38 @@ struct PlateParams {
     int *abort_flag;
     long long wait_limit;
     int debug_flags;
+};
+
+// One (plate, stress mode) of the directional-derivative contraction.
+struct DirUnit {
+    int inst;
+    int kl;            // internal stress index within the plate
+    int c, mc, kpos;   // class layout: class, chunk size, position in the chunk
+    int pad;
+    long long off;     // class layout: float offset of the chunk's dH super-blocks
+};
+
+// Class layout: all stress modes of class c of one plate against row class a.
+struct DirGroup {
+    int inst, c, a;
+    int unit0, nk;     // the class-c stress modes: units[unit0 .. unit0 + nk)
+    int pad;
+};
+
+struct DirParams {
+    const InstDesc *inst;
+    const DirUnit *units;
+    const DirGroup *groups;
+    int n_groups;
+    const float *dH;
+    const int *perm;
+    const float *kappa;
+    const float *seg_q;           // [(steps+1)][total_modes]
+    const float *seg_w;           // [steps][total_modes]
+    const float *xe;              // [steps][2][total_k]
+    double *dir_acc;              // [total_k][4] (class layout: one slot per row class)
+    int steps;
+    long long total_modes, total_k;
 };
 
 struct TensionParams {
@@ -208,10 +242,12 @@ struct GradEpilogue {
     int n_inst;
     long long total_modes, total_k;
     const double *omega2, *gamma, *dt;  // per mode FP64
-    const float *adj, *gacc, *kacc, *diracc, *tacc;
+    const float *adj, *gacc, *kacc, *tacc;
+    const double *dir_acc;
     const int *kperm;                   // internal stress index -> user index (per plate)
     double *d_omega2, *d_gamma, *d_b, *d_c, *d_q0, *d_qm1, *d_tau, *d_kappa, *d_dir;
 };
 cudaError_t launch_grad_epilogue(const GradEpilogue &g, int max_n, cudaStream_t s);
+cudaError_t launch_dir_contract(const DirParams &p, int n_units, cudaStream_t s);
 
 }  // namespace mdx

@@ -95,8 +95,8 @@ struct mdx_plan {
         cudaEvent_t a, b;
     };
     std::vector<Rec> recs;
-    long stat_launch[3] = {0, 0, 0};
-    double stat_ms[3] = {0, 0, 0}, stat_bytes[3] = {0, 0, 0};
+    long stat_launch[4] = {0, 0, 0, 0};
+    double stat_ms[4] = {0, 0, 0, 0}, stat_bytes[4] = {0, 0, 0, 0};
     double H_bytes_per_step = 0, dH_bytes_per_step = 0;
     int smem_optin = 0;
     // symmetry-class layout
@@ -105,6 +105,11 @@ struct mdx_plan {
     int min_stage_floats = 4;
     ParityChunk *d_chunks = nullptr;
     int *d_perm = nullptr, *d_kperm = nullptr;
+    // directional-derivative contraction units (plates planned with dH)
+    DirUnit *d_dir_units = nullptr;
+    int n_dir_units = 0;
+    DirGroup *d_dir_groups = nullptr;
+    int n_dir_groups = 0;
 };
 
 namespace {
@@ -652,6 +657,64 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
             if ((rc2 = upload(p, &p->d_perm, perm_all.data(), perm_all.size()))) return bail(rc2);
             if ((rc2 = upload(p, &p->d_kperm, kperm_all.data(), kperm_all.size()))) return bail(rc2);
             if ((rc2 = upload(p, &p->d_chunks, chunks.data(), chunks.size()))) return bail(rc2);
+            std::vector<DirUnit> units;
+            if (parity) {
+                for (const auto &it : items) {
+                    if (!p->inst[it.inst].has_dir) continue;
+                    for (int ci = it.chunk0; ci < it.chunk1; ++ci)
+                        for (int q = 0; q < chunks[ci].mc; ++q) {
+                            DirUnit u{};
+                            u.inst = it.inst;
+                            u.kl = chunks[ci].kl0 + q;
+                            u.c = chunks[ci].c;
+                            u.mc = chunks[ci].mc;
+                            u.kpos = q;
+                            u.off = chunks[ci].doff;
+                            units.push_back(u);
+                        }
+                }
+            } else {
+                for (int i = 0; i < n_inst; ++i) {
+                    const InstDesc &d = p->inst[i];
+                    if (!d.has_dir) continue;
+                    for (int k = 0; k < d.M; ++k) {
+                        DirUnit u{};
+                        u.inst = i;
+                        u.kl = k;
+                        u.mc = 1;
+                        units.push_back(u);
+                    }
+                }
+            }
+            std::stable_sort(units.begin(), units.end(), [](const DirUnit &x, const DirUnit &y) {
+                return x.inst != y.inst ? x.inst < y.inst : x.kl < y.kl;
+            });
+            std::vector<DirGroup> groups;
+            if (parity) {
+                // class-c stress modes of a plate are contiguous in internal order
+                size_t u0 = 0;
+                while (u0 < units.size()) {
+                    size_t u1 = u0;
+                    while (u1 < units.size() && units[u1].inst == units[u0].inst &&
+                           units[u1].c == units[u0].c)
+                        ++u1;
+                    for (int a = 0; a < 4; ++a) {
+                        DirGroup gr{};
+                        gr.inst = units[u0].inst;
+                        gr.c = units[u0].c;
+                        gr.a = a;
+                        gr.unit0 = (int)u0;
+                        gr.nk = (int)(u1 - u0);
+                        const InstDesc &d = p->inst[gr.inst];
+                        if (d.ncls[a] > 0 && d.ncls[a ^ gr.c] > 0) groups.push_back(gr);
+                    }
+                    u0 = u1;
+                }
+            }
+            p->n_dir_units = (int)units.size();
+            p->n_dir_groups = (int)groups.size();
+            if ((rc2 = upload(p, &p->d_dir_units, units.data(), units.size()))) return bail(rc2);
+            if ((rc2 = upload(p, &p->d_dir_groups, groups.data(), groups.size()))) return bail(rc2);
         }
         p->min_stage_floats = p->npad_max;
         if (parity) {
@@ -704,7 +767,8 @@ int configure_tiles(mdx_plan *p, int stage_req, int ring_req) {
     stage = (stage + 15) & ~15;
     bool dir = false;
     for (const auto &d : p->inst) dir = dir || d.has_dir;
-    const int us_fwd = 1, us_rev = dir ? 3 : 2;
+    const int us_fwd = 1, us_rev = 2;
+    (void)dir;
     auto ufl = [&](int us) {
         // partial sums: dense row groups [kChunkK][slots][1024]; class chunks
         // [mc][u, z][N_pad] (the direction pass needs no stored vector)
@@ -802,8 +866,7 @@ int run_segment(mdx_plan *p, PlateParams &P, TensionParams &T, cudaStream_t s) {
         mdx_plan::Rec rec{};
         if (p->profiling) {
             rec.which = P.mode;
-            rec.bytes = (double)P.steps * (p->H_bytes_per_step +
-                                           (P.mode == MODE_REVERSE ? p->dH_bytes_per_step : 0.0));
+            rec.bytes = (double)P.steps * p->H_bytes_per_step;
             MDX_CUDA(cudaEventCreate(&rec.a), "event");
             MDX_CUDA(cudaEventCreate(&rec.b), "event");
             MDX_CUDA(cudaEventRecord(rec.a, s), "event");
@@ -849,7 +912,8 @@ extern "C" int mdx_simulate(mdx_plan *p, const float *exc, const double *q0, con
 namespace {
 
 struct GradWork {
-    float *seg_q, *seg_v, *adj, *gacc, *kacc, *diracc, *tacc;
+    float *seg_q, *seg_v, *adj, *gacc, *kacc, *tacc, *seg_w, *xe;
+    double *dir_acc;
     size_t bytes;
 };
 
@@ -869,8 +933,11 @@ GradWork grad_layout(const mdx_plan *p, int K, void *base) {
     w.adj = take(AD_N * TM);
     w.gacc = take(2 * GA_N * TM);
     w.kacc = take(2 * TK);
-    w.diracc = take(2 * TK);
     w.tacc = take(2 * (size_t)p->n_inst);
+    const bool dir = p->n_dir_units > 0;
+    w.seg_w = dir ? take((size_t)K * TM) : nullptr;
+    w.xe = dir ? take((size_t)K * 2 * TK) : nullptr;
+    w.dir_acc = reinterpret_cast<double *>(take(8 * TK));
     w.bytes = off;
     return w;
 }
@@ -902,7 +969,7 @@ extern "C" int mdx_grad(mdx_plan *p, const float *exc, const double *q0, const d
     const size_t TM = (size_t)p->total_modes, TK = (size_t)std::max<long long>(p->total_k, 1);
     MDX_CUDA(cudaMemsetAsync(w.gacc, 0, 2 * GA_N * TM * sizeof(float), s), "memset");
     MDX_CUDA(cudaMemsetAsync(w.kacc, 0, 2 * TK * sizeof(float), s), "memset");
-    MDX_CUDA(cudaMemsetAsync(w.diracc, 0, 2 * TK * sizeof(float), s), "memset");
+    MDX_CUDA(cudaMemsetAsync(w.dir_acc, 0, 4 * TK * sizeof(double), s), "memset");
     MDX_CUDA(cudaMemsetAsync(w.tacc, 0, 2 * p->n_inst * sizeof(float), s), "memset");
     MDX_CUDA(launch_init_adjoint(p->d_inst, p->n_inst, p->coef.c, d_audio, steps, w.adj,
                                  p->total_modes, 0, s),
@@ -931,10 +998,41 @@ extern "C" int mdx_grad(mdx_plan *p, const float *exc, const double *q0, const d
         P.adj = T.adj = w.adj;
         P.gacc = T.gacc = w.gacc;
         P.kacc = w.kacc;
-        P.diracc = w.diracc;
+        P.seg_w = w.seg_w;
+        P.xe = w.xe;
+        P.total_k = p->total_k;
         T.tacc = w.tacc;
         rc = run_segment(p, P, T, s);
         if (rc) return rc;
+        if (p->n_dir_units > 0) {
+            DirParams D{};
+            D.inst = p->d_inst;
+            D.units = p->d_dir_units;
+            D.groups = p->parity ? p->d_dir_groups : nullptr;
+            D.n_groups = p->parity ? p->n_dir_groups : 0;
+            D.dH = p->d_dH;
+            D.perm = p->d_perm;
+            D.kappa = p->d_kappa;
+            D.seg_q = w.seg_q;
+            D.seg_w = w.seg_w;
+            D.xe = w.xe;
+            D.dir_acc = w.dir_acc;
+            D.steps = L;
+            D.total_modes = p->total_modes;
+            D.total_k = p->total_k;
+            mdx_plan::Rec rec{};
+            if (p->profiling) {
+                rec.which = 3;
+                MDX_CUDA(cudaEventCreate(&rec.a), "event");
+                MDX_CUDA(cudaEventCreate(&rec.b), "event");
+                MDX_CUDA(cudaEventRecord(rec.a, s), "event");
+            }
+            MDX_CUDA(launch_dir_contract(D, p->n_dir_units, s), "direction contraction");
+            if (p->profiling) {
+                MDX_CUDA(cudaEventRecord(rec.b, s), "event");
+                p->recs.push_back(rec);
+            }
+        }
     }
     GradEpilogue g{};
     g.inst = p->d_inst;
@@ -947,7 +1045,7 @@ extern "C" int mdx_grad(mdx_plan *p, const float *exc, const double *q0, const d
     g.adj = w.adj;
     g.gacc = w.gacc;
     g.kacc = w.kacc;
-    g.diracc = w.diracc;
+    g.dir_acc = w.dir_acc;
     g.tacc = w.tacc;
     g.kperm = p->d_kperm;
     if (out) {
@@ -1014,14 +1112,14 @@ extern "C" int mdx_plan_reset_stats(mdx_plan *p) {
         cudaEventDestroy(r.b);
     }
     p->recs.clear();
-    for (int i = 0; i < 3; ++i) p->stat_launch[i] = 0, p->stat_ms[i] = 0, p->stat_bytes[i] = 0;
+    for (int i = 0; i < 4; ++i) p->stat_launch[i] = 0, p->stat_ms[i] = 0, p->stat_bytes[i] = 0;
     return MDX_OK;
 }
 
 extern "C" int mdx_plan_kernel_stats(mdx_plan *p, int which, long *launches, double *ms,
                                      double *bytes) {
     if (!p) return fail(MDX_ERR_ARG, "plan is NULL");
-    if (which < 0 || which > 2) return fail(MDX_ERR_ARG, "which must be 0, 1 or 2");
+    if (which < 0 || which > 3) return fail(MDX_ERR_ARG, "which must be 0..3");
     for (auto &r : p->recs) {
         MDX_CUDA(cudaEventSynchronize(r.b), "event sync");
         float t = 0.f;

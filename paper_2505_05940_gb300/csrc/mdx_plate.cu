@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                     const PlateItem item = P.items[ii];
                     const InstDesc d = P.inst[item.inst];
                     const int rows_per_stage = max(1, stage_floats / d.Npad);
-                    const int nmat = (reverse && d.has_dir) ? 2 : 1;
+                    const int nmat = 1;   // the direction tensor is contracted per segment (mdx_dir.cu)
                     if constexpr (PAR) {
                         // class chunks: super-blocks a = 0..3, rows of mc * nb4 floats
                         for (int ci = item.chunk0; ci < item.chunk1 && ok; ++ci) {
@@ -323,8 +323,10 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                     st[ST_FLOC * Np + s] = 0.f;
                 } else {
                     const float qn = in ? P.seg_q[(long long)t_loc * TM + m] : 0.f;
+                    const float wv = in ? P.coef.r[m] * st[ST_QHI * Np + s] : 0.f;
                     st[ST_SRC0 * Np + s] = qn;
-                    st[ST_SRC1 * Np + s] = in ? P.coef.r[m] * st[ST_QHI * Np + s] : 0.f;
+                    st[ST_SRC1 * Np + s] = wv;
+                    if (in && item.owner && P.seg_w) P.seg_w[(long long)t_loc * TM + m] = wv;
                     st[ST_FLOC * Np + s] = 0.f;
                     st[ST_FLOC2 * Np + s] = 0.f;
                 }
@@ -363,7 +365,7 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
             const int g = tid / ncol4, c4 = tid - (tid / ncol4) * ncol4;
             const bool active = g < G;
             const int rows_per_stage = max(1, stage_floats / Np);
-            const int nmat = (reverse && d.has_dir) ? 2 : 1;
+            const int nmat = 1;   // the direction tensor is contracted per segment (mdx_dir.cu)
             const float *src0 = reverse ? st + ST_SRC0 * Np : st + ST_QHI * Np;
             const float *src1 = st + ST_SRC1 * Np;
             const int spt = (Np + kPlateThreads - 1) / kPlateThreads;
@@ -498,13 +500,11 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                             kahan_add(s0, c0, -eta * xi);
                             ka[0] = s0;
                             ka[1] = c0;
-                            if (d.has_dir) {
-                                float *da = P.diracc + 2 * kk;
-                                float s1 = da[0], c1 = da[1];
-                                kahan_add(s1, c1, -kap * fmaf(xi, red[q * 4 + 2], eta * red[q * 4 + 3]));
-                                da[0] = s1;
-                                da[1] = c1;
+                            if (d.has_dir && P.xe) {
+                                P.xe[((long long)t_loc * 2 + 0) * P.total_k + kk] = xi;
+                                P.xe[((long long)t_loc * 2 + 1) * P.total_k + kk] = eta;
                             }
+                            (void)kap;
                         }
                     }
                     consumer_bar();
@@ -654,12 +654,9 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                         kahan_add(s0, c0, -dv[0] * dv[1]);
                         ka[0] = s0;
                         ka[1] = c0;
-                        if (d.has_dir) {
-                            float *da = P.diracc + 2 * (d.k_off + k);
-                            float s1 = da[0], c1 = da[1];
-                            kahan_add(s1, c1, -kap * fmaf(dv[1], dv[2], dv[0] * dv[3]));
-                            da[0] = s1;
-                            da[1] = c1;
+                        if (d.has_dir && P.xe) {
+                            P.xe[((long long)t_loc * 2 + 0) * P.total_k + d.k_off + k] = dv[1];
+                            P.xe[((long long)t_loc * 2 + 1) * P.total_k + d.k_off + k] = dv[0];
                         }
                     }
                 }
