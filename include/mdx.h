@@ -139,6 +139,18 @@ const char *mdx_version(void);
 int mdx_plan_create(mdx_plan **out, const mdx_instance *inst, int n_inst,
                     const mdx_options *opts);
 
+/*
+ * Replace the per-mode coefficients of a plan without rebuilding it (the
+ * coupling tensors and the work assignment stay): host FP64 arrays over all
+ * modes in plan order (omega2, gamma, b, c; NULL keeps the current values),
+ * tau [n_inst] (tension instances; NULL keeps) and kappa over all stress
+ * modes in plan order (NULL keeps).  Validated like mdx_plan_create; on error
+ * the plan is unchanged.  Synchronises the plan's device.
+ */
+int mdx_plan_set_coefficients(mdx_plan *plan, const double *omega2, const double *gamma,
+                              const double *b, const double *c, const double *tau,
+                              const double *kappa);
+
 /* Release every resource of the plan (synchronises its device first). */
 int mdx_plan_destroy(mdx_plan *plan);
 
@@ -239,6 +251,49 @@ int mdx_coeffs_from_physics(int n, const double *lambda, double D, double T0, do
 int mdx_coeffs_vjp(int n, const double *lambda, double D, double T0, double rho, double s0,
                    double s1, const double *d_omega2, const double *d_gamma, double *dD,
                    double *dT0, double *ds0, double *ds1, double *d_lambda);
+
+/*
+ * Learned proposal network (initial parameter estimates for inverse fitting).
+ * A multilayer perceptron d0 -> d1 -> ... -> dL with ReLU after every hidden
+ * layer and a linear output.  Weights BF16 (raw bit patterns, row-major
+ * [d_{l+1}][d_l]), biases FP32; every product accumulates in FP32 on the
+ * tensor cores; hidden activations are stored in BF16.  The paper has no
+ * network; this serves the learned initialisation of the inverse fits
+ * (Sec. 4.3.3 notes the fits' sensitivity to initialisation).  All pointers
+ * are device memory owned by the caller.
+ */
+#define MDX_MLP_MAX_LAYERS 8
+typedef struct mdx_mlp {
+    int n_layers;
+    int dims[MDX_MLP_MAX_LAYERS + 1];
+    const uint16_t *W[MDX_MLP_MAX_LAYERS];
+    const float *b[MDX_MLP_MAX_LAYERS];
+} mdx_mlp;
+
+/* Elements (uint16) of the hidden-activation buffer, and of the backward
+ * work buffer, for a batch. */
+size_t mdx_mlp_act_elems(const mdx_mlp *net, int batch);
+size_t mdx_mlp_work_elems(const mdx_mlp *net, int batch);
+
+/* y [batch][dL] (FP32) = net(x), x BF16 [batch][d0]; acts receives the hidden
+ * activations (needed by the backward pass). */
+int mdx_mlp_forward(const mdx_mlp *net, int batch, const uint16_t *x, uint16_t *acts, float *y,
+                    void *stream);
+
+/* Gradients of sum(dy . y) for the same x and acts: dW[l] FP32 [d_{l+1}][d_l],
+ * db[l] FP32 [d_{l+1}] (overwritten).  dy is rounded to BF16 once; the
+ * back-propagated signals are BF16 like the activations. */
+int mdx_mlp_backward(const mdx_mlp *net, int batch, const uint16_t *x, const uint16_t *acts,
+                     const float *dy, float *const *dW, float *const *db, uint16_t *work,
+                     void *stream);
+
+/* One Adam step on n FP32 master weights w (moments m, v; step number t >= 1),
+ * refreshing the BF16 copy w_bf16 (may be NULL). */
+int mdx_adam_step(long long n, float *w, uint16_t *w_bf16, const float *g, float *m, float *v,
+                  float lr, float beta1, float beta2, float eps, int t, void *stream);
+
+/* Round-to-nearest-even FP32 -> BF16 of n elements. */
+int mdx_f32_to_bf16(long long n, const float *x, uint16_t *y, void *stream);
 
 /*
  * Forward run of strings and membranes that allocates no device memory.

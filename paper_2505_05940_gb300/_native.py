@@ -26,7 +26,9 @@ EXPORTED = ("mdx_last_error", "mdx_version", "mdx_plan_create", "mdx_plan_destro
             "mdx_plan_info", "mdx_checkpoint_bytes", "mdx_simulate", "mdx_grad_workspace_bytes",
             "mdx_grad", "mdx_coeffs_from_physics", "mdx_coeffs_vjp", "mdx_plan_set_profiling",
             "mdx_plan_kernel_stats", "mdx_plan_reset_stats", "mdx_plan_configure",
-            "mdx_plan_tiles", "mdx_simulate_strings_noalloc")
+            "mdx_plan_tiles", "mdx_simulate_strings_noalloc", "mdx_plan_set_coefficients",
+            "mdx_mlp_act_elems", "mdx_mlp_work_elems", "mdx_mlp_forward", "mdx_mlp_backward",
+            "mdx_adam_step", "mdx_f32_to_bf16")
 
 
 class MdxError(RuntimeError):
@@ -52,6 +54,14 @@ class Options(ctypes.Structure):
                 ("ring_stages", ctypes.c_int), ("stage_bytes", ctypes.c_int),
                 ("force_split", ctypes.c_int), ("wait_limit", ctypes.c_int),
                 ("debug_flags", ctypes.c_int)]
+
+
+MLP_MAX_LAYERS = 8
+
+
+class MLPDesc(ctypes.Structure):
+    _fields_ = [("n_layers", ctypes.c_int), ("dims", ctypes.c_int * (MLP_MAX_LAYERS + 1)),
+                ("W", ctypes.c_void_p * MLP_MAX_LAYERS), ("b", ctypes.c_void_p * MLP_MAX_LAYERS)]
 
 
 class Grads(ctypes.Structure):
@@ -97,6 +107,17 @@ def load(build_if_missing: bool = True):
                                               _D, _D]
         L.mdx_coeffs_vjp.argtypes = [i32, _D, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, _D, _D, _D, _D, _D, _D, _D]
+        L.mdx_plan_set_coefficients.argtypes = [vp, _D, _D, _D, _D, _D, _D]
+        L.mdx_mlp_act_elems.argtypes = [ctypes.POINTER(MLPDesc), i32]
+        L.mdx_mlp_act_elems.restype = sz
+        L.mdx_mlp_work_elems.argtypes = [ctypes.POINTER(MLPDesc), i32]
+        L.mdx_mlp_work_elems.restype = sz
+        L.mdx_mlp_forward.argtypes = [ctypes.POINTER(MLPDesc), i32, vp, vp, vp, vp]
+        L.mdx_mlp_backward.argtypes = [ctypes.POINTER(MLPDesc), i32, vp, vp, vp,
+                                       ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp]
+        L.mdx_adam_step.argtypes = [ctypes.c_longlong, vp, vp, vp, vp, vp, ctypes.c_float,
+                                    ctypes.c_float, ctypes.c_float, ctypes.c_float, i32, vp]
+        L.mdx_f32_to_bf16.argtypes = [ctypes.c_longlong, vp, vp, vp]
         L.mdx_plan_configure.argtypes = [vp, i32, i32]
         L.mdx_plan_tiles.argtypes = [vp] + [ctypes.POINTER(i32)] * 4
         L.mdx_plan_set_profiling.argtypes = [vp, i32]
@@ -216,6 +237,19 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    # ------------------------------------------------------------------ coefficients
+    def set_coefficients(self, omega2=None, gamma=None, b=None, c=None, tau=None, kappa=None):
+        """Host FP64 arrays in plan order (None keeps the current values)."""
+        def dp(x):
+            if x is None:
+                return None
+            a = np.ascontiguousarray(x, dtype=np.float64)
+            keep.append(a)
+            return a.ctypes.data_as(_D)
+        keep = []
+        check(load().mdx_plan_set_coefficients(self._h, dp(omega2), dp(gamma), dp(b), dp(c),
+                                               dp(tau), dp(kappa)))
 
     # ------------------------------------------------------------------ tiles
     def configure(self, stage_bytes=0, ring_stages=0):

@@ -110,6 +110,10 @@ struct mdx_plan {
     int n_dir_units = 0;
     DirGroup *d_dir_groups = nullptr;
     int n_dir_groups = 0;
+    // host copies for coefficient updates
+    std::vector<double> h_omega2, h_gamma, h_b, h_c, h_tau, h_kappa;
+    std::vector<int> h_kperm;      // internal stress index -> user index, concatenated
+    float *d_coef_all = nullptr;   // the 7 FP32 coefficient arrays
 };
 
 namespace {
@@ -291,6 +295,18 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
         p->inst[i] = d;
     }
     const size_t TM = (size_t)p->total_modes;
+    for (int i = 0; i < n_inst; ++i) {
+        const mdx_instance &S = I[i];
+        for (int m = 0; m < S.n_phi; ++m) {
+            p->h_b.push_back(S.b[m]);
+            p->h_c.push_back(S.c[m]);
+        }
+        p->h_tau.push_back(S.kind == MDX_KIND_TENSION ? S.tau : 0.0);
+        const int M = (S.kind == MDX_KIND_PLATE) ? S.n_psi : 0;
+        for (int k = 0; k < M; ++k) p->h_kappa.push_back(S.kappa[k]);
+    }
+    p->h_omega2 = w2d;
+    p->h_gamma = gmd;
     {
         std::vector<float> all;
         all.reserve(7 * TM);
@@ -298,6 +314,7 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
         float *dc = nullptr;
         int rc = upload(p, &dc, all.data(), all.size());
         if (rc) return bail(rc);
+        p->d_coef_all = dc;
         p->coef.eps = dc;
         p->coef.rw2 = dc + TM;
         p->coef.r = dc + 2 * TM;
@@ -648,6 +665,7 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
             std::vector<int> perm_all, kperm_all;
             for (int i = 0; i < n_inst; ++i) {
                 InstDesc &d = p->inst[i];
+                for (int kk = 0; kk < d.M; ++kk) p->h_kperm.push_back(kperm[i][kk]);
                 for (int kk = 0; kk < d.M; ++kk) kap2.push_back((float)I[i].kappa[kperm[i][kk]]);
                 d.perm_off = (long long)perm_all.size();
                 for (int v : perm[i]) perm_all.push_back(v);
@@ -1153,5 +1171,84 @@ extern "C" int mdx_plan_tiles(const mdx_plan *p, int *stage_bytes, int *ring_fwd
     if (ring_fwd) *ring_fwd = p->ring_fwd;
     if (ring_rev) *ring_rev = p->ring_rev;
     if (ctas) *ctas = p->n_cta;
+    return MDX_OK;
+}
+
+extern "C" int mdx_plan_set_coefficients(mdx_plan *p, const double *omega2, const double *gamma,
+                                         const double *b, const double *c, const double *tau,
+                                         const double *kappa) {
+    if (!p) return fail(MDX_ERR_ARG, "plan is NULL");
+    const size_t TM = (size_t)p->total_modes;
+    std::vector<double> w2 = omega2 ? std::vector<double>(omega2, omega2 + TM) : p->h_omega2;
+    std::vector<double> gm = gamma ? std::vector<double>(gamma, gamma + TM) : p->h_gamma;
+    std::vector<double> bb = b ? std::vector<double>(b, b + TM) : p->h_b;
+    std::vector<double> cc = c ? std::vector<double>(c, c + TM) : p->h_c;
+    std::vector<double> tt = tau ? std::vector<double>(tau, tau + p->n_inst) : p->h_tau;
+    std::vector<double> kp = kappa ? std::vector<double>(kappa, kappa + p->total_k) : p->h_kappa;
+    for (int i = 0; i < p->n_inst; ++i) {
+        const InstDesc &d = p->inst[i];
+        const double T = p->dt[i];
+        for (int m = 0; m < d.N; ++m) {
+            const size_t g = d.mode_off + m;
+            if (!std::isfinite(w2[g]) || !std::isfinite(gm[g]) || !std::isfinite(bb[g]) || !std::isfinite(cc[g]))
+                return fail(MDX_ERR_NONFINITE, "instance %d mode %d: non-finite coefficient", i, m);
+            if (!(w2[g] > 0.0)) return fail(MDX_ERR_ARG, "instance %d mode %d: omega2 must be > 0", i, m);
+            if (gm[g] < 0.0) return fail(MDX_ERR_UNSTABLE, "instance %d mode %d: gamma < 0", i, m);
+            if (std::sqrt(w2[g]) * T >= 2.0)
+                return fail(MDX_ERR_UNSTABLE, "instance %d mode %d: omega*dt = %.4f >= 2", i, m,
+                            std::sqrt(w2[g]) * T);
+        }
+        if (!std::isfinite(tt[i]) || tt[i] < 0.0) return fail(MDX_ERR_ARG, "instance %d: tau must be finite and >= 0", i);
+    }
+    for (double v : kp)
+        if (!std::isfinite(v)) return fail(MDX_ERR_NONFINITE, "non-finite kappa");
+    std::vector<float> eps(TM), rw2(TM), rr(TM), bf(TM), cf(TM), rwl(TM);
+    for (int i = 0; i < p->n_inst; ++i) {
+        const InstDesc &d = p->inst[i];
+        const double T = p->dt[i];
+        for (int m = 0; m < d.N; ++m) {
+            const size_t g = d.mode_off + m;
+            const double den = 1.0 + gm[g] * T;
+            const double r = T * T / den;
+            const double rw = r * w2[g];
+            eps[g] = (float)(2.0 * gm[g] * T / den);
+            rw2[g] = (float)rw;
+            rwl[g] = (float)(rw - (double)(float)rw);
+            rr[g] = (float)r;
+            bf[g] = (float)bb[g];
+            cf[g] = (float)cc[g];
+        }
+    }
+    MDX_CUDA(cudaSetDevice(p->device), "cudaSetDevice");
+    MDX_CUDA(cudaDeviceSynchronize(), "synchronise");
+    float *dc = p->d_coef_all;
+    MDX_CUDA(cudaMemcpy(dc, eps.data(), TM * 4, cudaMemcpyHostToDevice), "upload");
+    MDX_CUDA(cudaMemcpy(dc + TM, rw2.data(), TM * 4, cudaMemcpyHostToDevice), "upload");
+    MDX_CUDA(cudaMemcpy(dc + 2 * TM, rr.data(), TM * 4, cudaMemcpyHostToDevice), "upload");
+    MDX_CUDA(cudaMemcpy(dc + 3 * TM, bf.data(), TM * 4, cudaMemcpyHostToDevice), "upload");
+    MDX_CUDA(cudaMemcpy(dc + 4 * TM, cf.data(), TM * 4, cudaMemcpyHostToDevice), "upload");
+    MDX_CUDA(cudaMemcpy(dc + 6 * TM, rwl.data(), TM * 4, cudaMemcpyHostToDevice), "upload");
+    MDX_CUDA(cudaMemcpy(p->d_omega2, w2.data(), TM * 8, cudaMemcpyHostToDevice), "upload");
+    MDX_CUDA(cudaMemcpy(p->d_gamma, gm.data(), TM * 8, cudaMemcpyHostToDevice), "upload");
+    // tau lives in the instance table; kappa in internal (class-sorted) order
+    for (int i = 0; i < p->n_inst; ++i) p->inst[i].taup = (p->inst[i].kind == MDX_KIND_TENSION) ? (float)tt[i] : 0.f;
+    MDX_CUDA(cudaMemcpy(p->d_inst, p->inst.data(), p->inst.size() * sizeof(InstDesc), cudaMemcpyHostToDevice), "upload");
+    if (p->total_k > 0 && p->d_kappa) {
+        std::vector<float> k2(p->total_k);
+        for (int i = 0; i < p->n_inst; ++i) {
+            const InstDesc &d = p->inst[i];
+            for (int kk = 0; kk < d.M; ++kk) {
+                const int ku = p->h_kperm.empty() ? kk : p->h_kperm[d.k_off + kk];
+                k2[d.k_off + kk] = (float)kp[d.k_off + ku];
+            }
+        }
+        MDX_CUDA(cudaMemcpy(p->d_kappa, k2.data(), p->total_k * 4, cudaMemcpyHostToDevice), "upload");
+    }
+    p->h_omega2 = w2;
+    p->h_gamma = gm;
+    p->h_b = bb;
+    p->h_c = cc;
+    p->h_tau = tt;
+    p->h_kappa = kp;
     return MDX_OK;
 }

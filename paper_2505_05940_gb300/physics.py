@@ -124,7 +124,10 @@ def prepare(inst, fs, steps, coupling="auto", want_aspect_derivative=False):
         if inst.nonlinear and M > 0 and coupling is not None:
             psi_cls = None
             if callable(coupling):
-                H, zeta4 = coupling(inst, labels, M)
+                res = coupling(inst, labels, M)
+                H, zeta4 = res[0], res[1]
+                if len(res) > 2:
+                    psi_cls = res[2]
                 dH = dz = None
             elif want_aspect_derivative:
                 H, zeta4, dH, dz, psi_cls = _coupling.coupling_with_aspect_derivative(

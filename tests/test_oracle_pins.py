@@ -506,3 +506,61 @@ def test_adjoint_matches_central_fd(kind):
             checks.append((g, _fd(oi, ybar, sh, 1e-4 * np.abs(oi.H[k]).max())))
     for got, ref in checks:
         assert abs(got - ref) <= 1e-6 * abs(ref) + 1e-9 * max(abs(c[1]) for c in checks), (got, ref)
+
+
+# ---------------------------------------------------------------- proposal MLP oracle
+
+def _mlp(rng, dims):
+    Ws = [rng.normal(size=(dims[l + 1], dims[l])) / np.sqrt(dims[l]) for l in range(len(dims) - 1)]
+    bs = [rng.normal(size=dims[l + 1]) * 0.1 for l in range(len(dims) - 1)]
+    return Ws, bs
+
+
+def test_mlp_oracle_backward_matches_fd():
+    from oracle import mlp_oracle as MO
+    rng = np.random.default_rng(3)
+    dims = [12, 9, 7, 5]
+    Ws, bs = _mlp(rng, dims)
+    x = rng.normal(size=(6, 12))
+    dy = rng.normal(size=(6, 5))
+    y, hs = MO.forward(Ws, bs, x, bf16=False)
+    dWs, dbs = MO.backward(Ws, bs, hs, dy, bf16=False)
+    L = lambda W2, b2: float(np.sum(dy * MO.forward(W2, b2, x, bf16=False)[0]))
+    h = 1e-6
+    for l in range(3):
+        for (i, j) in ((0, 0), (2, 3), (4, 1)):
+            if i >= dims[l + 1] or j >= dims[l]:
+                continue
+            Wp = [w.copy() for w in Ws]; Wp[l][i, j] += h
+            Wm = [w.copy() for w in Ws]; Wm[l][i, j] -= h
+            fd = (L(Wp, bs) - L(Wm, bs)) / (2 * h)
+            assert abs(dWs[l][i, j] - fd) <= 1e-6 * max(1.0, abs(fd))
+        bp = [b.copy() for b in bs]; bp[l][1] += h
+        bm = [b.copy() for b in bs]; bm[l][1] -= h
+        fd = (L(Ws, bp) - L(Ws, bm)) / (2 * h)
+        assert abs(dbs[l][1] - fd) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_bf16_rounding_is_round_to_nearest_even():
+    from oracle import mlp_oracle as MO
+    # 1 + 2^-8 is exactly halfway between 1 and 1 + 2^-7 in BF16: ties to even -> 1
+    assert MO.bf16_round(1.0 + 2.0 ** -8) == 1.0
+    assert MO.bf16_round(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6
+    assert MO.bf16_round(-3.0) == -3.0
+    v = np.array([0.1, 1 / 3, 1e-3, 123.456])
+    r = MO.bf16_round(v)
+    assert np.all(np.abs(r - v) <= np.abs(v) * 2.0 ** -8)
+
+
+def test_mlp_oracle_exact_on_small_integers():
+    """With small integer weights and inputs every BF16 rounding is exact, so
+    the BF16-emulating oracle equals plain integer arithmetic."""
+    from oracle import mlp_oracle as MO
+    rng = np.random.default_rng(5)
+    dims = [8, 6, 4]
+    Ws = [rng.integers(-3, 4, size=(dims[l + 1], dims[l])).astype(float) for l in range(2)]
+    bs = [rng.integers(-2, 3, size=dims[l + 1]).astype(float) for l in range(2)]
+    x = rng.integers(-2, 3, size=(5, 8)).astype(float)
+    y, _ = MO.forward(Ws, bs, x, bf16=True)
+    h = np.maximum(x @ Ws[0].T + bs[0], 0)
+    np.testing.assert_array_equal(y, h @ Ws[1].T + bs[1])
