@@ -114,7 +114,9 @@ typedef struct mdx_options {
     int wait_limit;    /* >0: spin-iteration cap of device waits (tests); 0 = default */
     int debug_flags;   /* bit 0: the second contributor of every shared plate withholds its
                           arrival, so the other contributors' bounded waits run out and the
-                          call reports MDX_ERR_TIMEOUT (fault-path tests); 0 in normal use */
+                          call reports MDX_ERR_TIMEOUT (fault-path tests);
+                          bit 1: run the gradient as separate recompute and reverse launches
+                          instead of the fused sweep (equivalence tests); 0 in normal use */
 } mdx_options;
 
 typedef struct mdx_plan mdx_plan;
@@ -199,7 +201,10 @@ size_t mdx_grad_workspace_bytes(const mdx_plan *plan, int steps, int K);
  * Reverse-mode derivative of a scalar loss L(y) through the whole time loop.
  * Given dL/dy it runs the adjoint recursion backwards, segment by segment:
  * each K-step segment is recomputed from the checkpoint mdx_simulate wrote
- * (same arguments, same K), then swept in reverse.
+ * (same arguments, same K), then swept in reverse.  With the class layout the
+ * recompute of segment s-1 runs in the same launch, and the same pass over
+ * the coupling tensor per step, as the reverse sweep of segment s; the
+ * results are bitwise those of separate launches.
  *   exc, q0, qm1, steps  as passed to mdx_simulate
  *   d_audio  device [n_inst][steps] FP32 dL/dy^n
  *   K, ckpt  the checkpoint interval and buffer filled by mdx_simulate
@@ -220,6 +225,19 @@ int mdx_grad(mdx_plan *plan, const float *exc, const double *q0, const double *q
  * and reverse launches, and the number of persistent CTAs.
  */
 int mdx_plan_configure(mdx_plan *plan, int stage_bytes, int ring_stages);
+
+/*
+ * L2 residency of the coupling stream.  Every step re-reads the whole
+ * coupling tensor; the plate kernel's bulk copies carry an L2 policy that
+ * gives a fraction of those addresses evict_last priority (the rest
+ * evict_first), so that when the tensors of the plan are about as large as
+ * the L2 (129 MB on GB300) that fraction stays resident across steps.
+ * fraction in [0, 1] (0 = no hint), or negative for the default: all of the
+ * stream when it fits in 70 % of the L2, else the share that does.  Results
+ * do not depend on it.  mdx_plan_l2_keep returns the fraction in use.
+ */
+int mdx_plan_set_l2_keep(mdx_plan *plan, double fraction);
+double mdx_plan_l2_keep(const mdx_plan *plan);
 int mdx_plan_tiles(const mdx_plan *plan, int *stage_bytes, int *ring_fwd, int *ring_rev,
                    int *ctas);
 
@@ -228,10 +246,11 @@ int mdx_plan_tiles(const mdx_plan *plan, int *stage_bytes, int *ring_fwd, int *r
  * plan is bracketed by CUDA events on its launch stream.  mdx_plan_kernel_stats
  * synchronises those events and returns, for one launch class
  * (0 = forward, 1 = checkpoint recompute, 2 = reverse sweep, 3 = per-segment
- * contraction of the direction tensor), the number of
- * launches, their summed device time in ms and their summed algorithmic bytes
- * (coupling-tensor bytes each launch must stream: one pass over H per step,
- * plus one over dH per reverse step when a direction tensor is planned).
+ * contraction of the direction tensor, 4 = fused sweep: the adjoint of one
+ * segment and the recompute of the previous one in the same launch), the
+ * number of launches, their summed device time in ms and their summed
+ * algorithmic bytes (coupling-tensor bytes each launch must stream: one pass
+ * over H per step; the direction tensor is counted by class 3).
  * mdx_plan_reset_stats clears the counters.  Off by default.
  */
 int mdx_plan_set_profiling(mdx_plan *plan, int enable);

@@ -28,7 +28,7 @@ EXPORTED = ("mdx_last_error", "mdx_version", "mdx_plan_create", "mdx_plan_destro
             "mdx_plan_kernel_stats", "mdx_plan_reset_stats", "mdx_plan_configure",
             "mdx_plan_tiles", "mdx_simulate_strings_noalloc", "mdx_plan_set_coefficients",
             "mdx_mlp_act_elems", "mdx_mlp_work_elems", "mdx_mlp_forward", "mdx_mlp_backward",
-            "mdx_adam_step", "mdx_f32_to_bf16")
+            "mdx_adam_step", "mdx_f32_to_bf16", "mdx_plan_set_l2_keep", "mdx_plan_l2_keep")
 
 
 class MdxError(RuntimeError):
@@ -119,6 +119,9 @@ def load(build_if_missing: bool = True):
                                     ctypes.c_float, ctypes.c_float, ctypes.c_float, i32, vp]
         L.mdx_f32_to_bf16.argtypes = [ctypes.c_longlong, vp, vp, vp]
         L.mdx_plan_configure.argtypes = [vp, i32, i32]
+        L.mdx_plan_set_l2_keep.argtypes = [vp, ctypes.c_double]
+        L.mdx_plan_l2_keep.argtypes = [vp]
+        L.mdx_plan_l2_keep.restype = ctypes.c_double
         L.mdx_plan_tiles.argtypes = [vp] + [ctypes.POINTER(i32)] * 4
         L.mdx_plan_set_profiling.argtypes = [vp, i32]
         L.mdx_plan_reset_stats.argtypes = [vp]
@@ -254,6 +257,13 @@ class Plan:
     # ------------------------------------------------------------------ tiles
     def configure(self, stage_bytes=0, ring_stages=0):
         check(load().mdx_plan_configure(self._h, int(stage_bytes), int(ring_stages)))
+
+    def set_l2_keep(self, fraction=-1.0):
+        """Fraction of the coupling stream kept in L2 (negative: automatic)."""
+        check(load().mdx_plan_set_l2_keep(self._h, float(fraction)))
+
+    def l2_keep(self):
+        return float(load().mdx_plan_l2_keep(self._h))
 
     def tiles(self):
         v = [ctypes.c_int() for _ in range(4)]

@@ -36,6 +36,8 @@ enum KernelMode : int {
     MODE_FORWARD = 0,   // simulate: writes audio / checkpoints / final state
     MODE_RECOMPUTE = 1, // re-run one segment from a checkpoint, storing every state
     MODE_REVERSE = 2,   // adjoint sweep over one stored segment
+    MODE_FUSED = 4,     // adjoint sweep over segment s and recompute of segment s-1 in
+                        // one pass over the coupling tensor per step (class layout)
 };
 
 // Per-mode FP32 coefficients, concatenated over instances (struct of arrays).
@@ -96,7 +98,12 @@ enum StateArr : int {
     ST_SRC0, ST_SRC1,               // right-hand sides of the H pass (reverse: q^n, w)
     ST_FLOC2,                       // reverse: local partial force at q^n
     ST_QP, ST_WP,                   // parity layout: right-hand sides in class order
-    ST_NARR
+    ST_NARR,
+    // fused sweep only: the recompute state of the previous segment
+    ST_RQHI = ST_NARR, ST_RQLO, ST_RV, ST_RVLO,
+    ST_RFLOC,                       // local partial force at the recompute state
+    ST_RQP,                         // recompute state in class order
+    ST_NARR_FUSED
 };
 
 // Accumulators of the reverse sweep, per mode (compensated FP32 pairs).
@@ -144,6 +151,13 @@ struct PlateParams {
     float *ckpt;                  // [n_ckpt][4][total_modes]
     float *seg_q;                 // recompute/reverse: [(steps+1)][total_modes] q_hi^n
     float *seg_v;                 // recompute/reverse: [(steps+1)][total_modes] v^n
+    // fused sweep: the reverse covers rev_steps (<= steps) steps from n_begin and
+    // reads seg_q / seg_v; the recompute runs steps steps from rec_begin (a
+    // checkpoint) and writes rseg_q / rseg_v
+    int rev_steps;
+    int rec_begin;
+    float *rseg_q;
+    float *rseg_v;
     long long total_modes;
     // reverse I/O
     const float *ybar;            // [n_inst][total_steps]
@@ -161,6 +175,7 @@ struct PlateParams {
     int *abort_flag;
     long long wait_limit;
     int debug_flags;
+    float l2_keep;                // fraction of the coupling stream kept in L2 (0: no hint)
 };
 
 // One (plate, stress mode) of the directional-derivative contraction.

@@ -74,6 +74,10 @@ struct mdx_plan {
     int ring_fwd = 0, ring_rev = 0, stage_bytes = 0, u_slots_fwd = 1, u_slots_rev = 2;
     int u_floats_fwd = 0, u_floats_rev = 0;
     size_t smem_fwd = 0, smem_rev = 0;
+    // fused adjoint sweep (reverse of segment s + recompute of segment s-1)
+    bool fuse = false;
+    int ring_fused = 0, u_floats_fused = 0;
+    size_t smem_fused = 0;
     long long part_stride = 0;
     float *d_part = nullptr;
     unsigned *d_counters = nullptr;
@@ -95,10 +99,14 @@ struct mdx_plan {
         cudaEvent_t a, b;
     };
     std::vector<Rec> recs;
-    long stat_launch[4] = {0, 0, 0, 0};
-    double stat_ms[4] = {0, 0, 0, 0}, stat_bytes[4] = {0, 0, 0, 0};
+    long stat_launch[5] = {0, 0, 0, 0, 0};
+    double stat_ms[5] = {0, 0, 0, 0, 0}, stat_bytes[5] = {0, 0, 0, 0, 0};
     double H_bytes_per_step = 0, dH_bytes_per_step = 0;
     int smem_optin = 0;
+    // L2 residency of the coupling stream: requested fraction (< 0: automatic)
+    double l2_keep_req = -1.0;
+    float l2_keep = 0.f;
+    long long l2_bytes = 0;
     // symmetry-class layout
     bool parity = false;
     int mc_max = kParMcMax;
@@ -202,6 +210,7 @@ struct Piece {
 };
 
 int configure_tiles(mdx_plan *p, int stage_req, int ring_req);
+void update_l2_keep(mdx_plan *p);
 
 }  // namespace
 
@@ -344,6 +353,9 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
         int dev_sms = 0, smem_optin = 0;
         MDX_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, p->device), "attr");
         MDX_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device), "attr");
+        int l2 = 0;
+        MDX_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, p->device), "attr");
+        p->l2_bytes = l2;
         int max_cta = dev_sms;
         if (o.max_ctas > 0) max_cta = std::min(max_cta, o.max_ctas);
         // Symmetry-class layout: used when every coupled plate gives classes
@@ -409,6 +421,9 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
                 if (p->inst[i].M > 0) std::iota(kperm[i].begin(), kperm[i].end(), 0);
             }
         p->parity = parity;
+        // the fused adjoint sweep needs the class layout (disabled by debug flag bit 1)
+        p->fuse = parity && !(p->debug_flags & 2);
+        const int narr = parity ? ST_NARR_FUSED : ST_NARR;   // state arrays per item
         // bytes (floats) one internal stress mode streams per pass
         auto unit_cost = [&](int i, int kk) -> double {
             const InstDesc &d = p->inst[i];
@@ -436,7 +451,25 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
         const double target = total / G;
         std::vector<std::vector<Piece>> per(G);
         bool contiguous_ok = (o.force_split <= 0);
-        if (contiguous_ok) {
+        // chunk size of the class layout (also used by the split's cost model)
+        int npad_plates = 4;
+        for (int i = 0; i < n_inst; ++i)
+            if (p->inst[i].M > 0) npad_plates = std::max(npad_plates, p->inst[i].Npad);
+        int mc_glob = kParMcMax;
+        if (parity) {
+            for (int i = 0; i < n_inst; ++i) {
+                const InstDesc &d = p->inst[i];
+                if (d.M == 0) continue;
+                int nq = 1;
+                for (int a = 0; a < 4; ++a) nq = std::max(nq, nb4(d.ncls[a]) / 4);
+                const int cap = std::max(1, std::min(kParMcMax, 8192 / (2 * npad_plates)));
+                int mc = cap;
+                auto tpk = [](int m) { int t = 32; while (t > 1 && t * m > 256) t >>= 1; return t; };
+                while (mc > 1 && tpk(mc) * kParQmax < nq) --mc;
+                mc_glob = std::min(mc_glob, mc);
+            }
+        }
+        if (contiguous_ok && !parity) {
             double cum = 0.0;
             for (int i = 0; i < n_inst; ++i) {
                 const InstDesc &d = p->inst[i];
@@ -455,9 +488,74 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
                     }
                 }
             }
+        }
+        if (contiguous_ok && parity) {
+            // Class layout: a CTA's time is its bytes plus a fixed cost per class
+            // chunk (every super-block of a chunk is a full pass over its rows,
+            // whatever the chunk's size) and per plate item.  Cut the unit
+            // sequence greedily under a time bound and bisect the bound until
+            // the cuts fit in G CTAs (min-max contiguous partition).
+            const double beta = 65536.0, gamma = 16384.0;   // floats-equivalent
+            std::vector<std::pair<int, int>> units;
+            for (int i = 0; i < n_inst; ++i)
+                for (int k = 0; k < p->inst[i].M; ++k) units.push_back({i, k});
+            std::vector<int> cut(units.size(), 0);
+            auto greedy = [&](double T, bool record) {
+                int g = 0, prev_i = -1, prev_c = -1, run = 0;
+                double cur = 0.0;
+                bool empty = true;
+                for (size_t u = 0; u < units.size(); ++u) {
+                    const int i = units[u].first, k = units[u].second;
+                    const double c = unit_cost(i, k);
+                    bool new_item = empty || prev_i != i;
+                    bool new_chunk = new_item || kcls[i][k] != prev_c || run >= mc_glob;
+                    double delta = c + (new_chunk ? beta : 0.0) + (new_item ? gamma : 0.0);
+                    if (!empty && cur + delta > T) {
+                        ++g;
+                        cur = 0.0;
+                        new_item = new_chunk = true;
+                        delta = c + beta + gamma;
+                    }
+                    cur += delta;
+                    empty = false;
+                    run = new_chunk ? 1 : run + 1;
+                    prev_i = i;
+                    prev_c = kcls[i][k];
+                    if (record) cut[u] = g;
+                }
+                return g + 1;
+            };
+            double lo = 0.0, hi = 0.0;
+            for (const auto &u : units) {
+                const double c = unit_cost(u.first, u.second) + beta + gamma;
+                lo = std::max(lo, c);
+                hi += c;
+            }
+            if (greedy(lo, false) > G) {
+                for (int it = 0; it < 60 && hi - lo > 1e-6 * hi; ++it) {
+                    const double mid = 0.5 * (lo + hi);
+                    if (greedy(mid, false) <= G) hi = mid; else lo = mid;
+                }
+            } else {
+                hi = lo;
+            }
+            greedy(hi, true);
+            for (size_t u = 0; u < units.size(); ++u) {
+                const int i = units[u].first, k = units[u].second;
+                const double c = unit_cost(i, k);
+                auto &v = per[cut[u]];
+                if (!v.empty() && v.back().inst == i && v.back().k1 == k) {
+                    v.back().k1 = k + 1;
+                    v.back().cost += c;
+                } else {
+                    v.push_back({i, k, k + 1, c});
+                }
+            }
+        }
+        if (contiguous_ok) {
             for (int g = 0; g < G && contiguous_ok; ++g) {
                 int need = 0;
-                for (const Piece &q : per[g]) need += ST_NARR * p->inst[q.inst].Npad;
+                for (const Piece &q : per[g]) need += narr * p->inst[q.inst].Npad;
                 if (need > state_cap) contiguous_ok = false;
             }
         }
@@ -486,7 +584,7 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
             std::vector<int> sfl(G, 0);
             for (const Piece &pc : pieces) {
                 const InstDesc &d = p->inst[pc.inst];
-                const int need = ST_NARR * d.Npad;
+                const int need = narr * d.Npad;
                 int best = -1;
                 for (int g = 0; g < G; ++g) {
                     bool has = false;
@@ -530,7 +628,7 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
                 it.slot = (int)(std::find(cl.begin(), cl.end(), g) - cl.begin());
                 it.owner = (it.slot == 0) ? 1 : 0;
                 it.smem_state = soff;
-                soff += ST_NARR * d.Npad;
+                soff += narr * d.Npad;
                 items.push_back(it);
                 p->npad_max = std::max(p->npad_max, d.Npad);
             }
@@ -544,19 +642,7 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
         // class layout: per item, per class chunk, super-blocks in stream order.
         std::vector<ParityChunk> chunks;
         long long H_total = 0;
-        int mc_glob = kParMcMax;
         if (parity) {
-            for (int i = 0; i < n_inst; ++i) {
-                const InstDesc &d = p->inst[i];
-                if (d.M == 0) continue;
-                int nq = 1;
-                for (int a = 0; a < 4; ++a) nq = std::max(nq, nb4(d.ncls[a]) / 4);
-                const int cap = std::max(1, std::min(kParMcMax, 8192 / (2 * p->npad_max)));
-                int mc = cap;
-                auto tpk = [](int m) { int t = 32; while (t > 1 && t * m > 256) t >>= 1; return t; };
-                while (mc > 1 && tpk(mc) * kParQmax < nq) --mc;
-                mc_glob = std::min(mc_glob, mc);
-            }
             for (auto &it : items) {
                 const InstDesc &d = p->inst[it.inst];
                 it.chunk0 = (int)chunks.size();
@@ -749,6 +835,7 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
             const int rcc = configure_tiles(p, o.stage_bytes, o.ring_stages);
             if (rcc) return bail(rcc);
         }
+        update_l2_keep(p);
         int rc;
         if ((rc = upload(p, &p->d_items, items.data(), items.size()))) return bail(rc);
         if ((rc = upload(p, &p->d_cta_off, cta_off.data(), cta_off.size()))) return bail(rc);
@@ -785,22 +872,25 @@ int configure_tiles(mdx_plan *p, int stage_req, int ring_req) {
     stage = (stage + 15) & ~15;
     bool dir = false;
     for (const auto &d : p->inst) dir = dir || d.has_dir;
-    const int us_fwd = 1, us_rev = 2;
+    const int us_fwd = 1, us_rev = 2, us_fused = 3;
     (void)dir;
     auto ufl = [&](int us) {
         // partial sums: dense row groups [kChunkK][slots][1024]; class chunks
-        // [mc][u, z][N_pad] (the direction pass needs no stored vector)
-        return p->parity ? p->mc_max * 2 * p->npad_max : kChunkK * us * kUPartFloats;
+        // [mc][u, z, u'][N_pad] (the direction pass needs no stored vector)
+        if (p->parity) return p->mc_max * (us == us_fwd ? 2 : us) * p->npad_max;
+        return kChunkK * us * kUPartFloats;
     };
+    const int us_big = p->fuse ? us_fused : us_rev;
     if (stage_req <= 0) {
         while (stage > 16 * 1024 && stage / 2 >= min_stage &&
-               plate_smem_bytes(2, stage, ufl(us_rev), p->state_floats) + 1024 > (size_t)smem_optin)
+               plate_smem_bytes(2, stage, ufl(us_big), p->state_floats) + 1024 > (size_t)smem_optin)
             stage = ((stage / 2) + 15) & ~15;
     }
-    int ring_f = 0, ring_r = 0;
-    size_t smem_f = 0, smem_r = 0;
-    for (int which = 0; which < 2; ++which) {
-        const int us = which == 0 ? us_fwd : us_rev;
+    int rings[3] = {0, 0, 0};
+    size_t smems[3] = {0, 0, 0};
+    const int n_cfg = p->fuse ? 3 : 2;
+    for (int which = 0; which < n_cfg; ++which) {
+        const int us = which == 0 ? us_fwd : (which == 1 ? us_rev : us_fused);
         const size_t fixed = plate_smem_bytes(0, stage, ufl(us), p->state_floats);
         if (fixed + 2 * (size_t)stage + 1024 > (size_t)smem_optin)
             return fail(MDX_ERR_UNSUPPORTED, "plate kernel needs %zu B of shared memory (> %d)",
@@ -811,20 +901,38 @@ int configure_tiles(mdx_plan *p, int stage_req, int ring_req) {
         if (need > (size_t)smem_optin)
             return fail(MDX_ERR_UNSUPPORTED, "plate kernel needs %zu B of shared memory (> %d)",
                         need, smem_optin);
-        (which == 0 ? ring_f : ring_r) = ring;
-        (which == 0 ? smem_f : smem_r) = need;
+        rings[which] = ring;
+        smems[which] = need;
     }
-    MDX_CUDA(plate_set_smem_limit(std::max(smem_f, smem_r)), "cudaFuncSetAttribute");
+    MDX_CUDA(plate_set_smem_limit(std::max(smems[0], std::max(smems[1], smems[2]))),
+             "cudaFuncSetAttribute");
     p->stage_bytes = stage;
     p->u_slots_fwd = us_fwd;
     p->u_slots_rev = us_rev;
     p->u_floats_fwd = ufl(us_fwd);
     p->u_floats_rev = ufl(us_rev);
-    p->ring_fwd = ring_f;
-    p->ring_rev = ring_r;
-    p->smem_fwd = smem_f;
-    p->smem_rev = smem_r;
+    p->u_floats_fused = p->fuse ? ufl(us_fused) : 0;
+    p->ring_fwd = rings[0];
+    p->ring_rev = rings[1];
+    p->ring_fused = rings[2];
+    p->smem_fwd = smems[0];
+    p->smem_rev = smems[1];
+    p->smem_fused = smems[2];
     return MDX_OK;
+}
+
+// Fraction of the per-step coupling stream marked evict_last in L2.  The
+// automatic choice keeps about 70 % of the L2 for it (the rest serves the
+// state, checkpoint and segment traffic): all of it when it fits, else the
+// share that fits.
+void update_l2_keep(mdx_plan *p) {
+    if (p->l2_keep_req >= 0.0) {
+        p->l2_keep = (float)std::min(1.0, p->l2_keep_req);
+        return;
+    }
+    const double budget = 0.7 * (double)p->l2_bytes;
+    p->l2_keep = (p->H_bytes_per_step > 0.0)
+                     ? (float)std::min(1.0, budget / p->H_bytes_per_step) : 0.f;
 }
 
 PlateParams base_plate(mdx_plan *p, int mode, int steps, int n_begin, int total_steps) {
@@ -842,9 +950,11 @@ PlateParams base_plate(mdx_plan *p, int mode, int steps, int n_begin, int total_
     P.total_steps = total_steps;
     P.mode = mode;
     P.stage_bytes = p->stage_bytes;
-    P.ring_stages = (mode == MODE_REVERSE) ? p->ring_rev : p->ring_fwd;
-    P.u_slots = (mode == MODE_REVERSE) ? p->u_slots_rev : p->u_slots_fwd;
-    P.u_floats = (mode == MODE_REVERSE) ? p->u_floats_rev : p->u_floats_fwd;
+    P.ring_stages = (mode == MODE_FUSED) ? p->ring_fused
+                    : (mode == MODE_REVERSE) ? p->ring_rev : p->ring_fwd;
+    P.u_slots = (mode == MODE_FUSED) ? 3 : (mode == MODE_REVERSE) ? p->u_slots_rev : p->u_slots_fwd;
+    P.u_floats = (mode == MODE_FUSED) ? p->u_floats_fused
+                 : (mode == MODE_REVERSE) ? p->u_floats_rev : p->u_floats_fwd;
     P.parity = p->parity ? 1 : 0;
     P.npad_max = p->npad_max;
     P.chunks = p->d_chunks;
@@ -858,6 +968,7 @@ PlateParams base_plate(mdx_plan *p, int mode, int steps, int n_begin, int total_
     P.abort_flag = p->d_abort;
     P.wait_limit = p->wait_limit;
     P.debug_flags = p->debug_flags;
+    P.l2_keep = p->l2_keep;
     return P;
 }
 
@@ -875,27 +986,31 @@ TensionParams base_tension(mdx_plan *p, int mode, int steps, int n_begin, int to
     return T;
 }
 
-int run_segment(mdx_plan *p, PlateParams &P, TensionParams &T, cudaStream_t s) {
-    if (!p->tension.empty()) MDX_CUDA(launch_tension(T, p->tension_max_n, s), "tension kernel");
-    if (p->any_plate) {
-        MDX_CUDA(cudaMemsetAsync(p->d_counters, 0, p->n_inst * sizeof(unsigned), s), "memset");
-        MDX_CUDA(cudaMemsetAsync(p->d_abort, 0, sizeof(int), s), "memset");
-        const size_t smem = (P.mode == MODE_REVERSE) ? p->smem_rev : p->smem_fwd;
-        mdx_plan::Rec rec{};
-        if (p->profiling) {
-            rec.which = P.mode;
-            rec.bytes = (double)P.steps * p->H_bytes_per_step;
-            MDX_CUDA(cudaEventCreate(&rec.a), "event");
-            MDX_CUDA(cudaEventCreate(&rec.b), "event");
-            MDX_CUDA(cudaEventRecord(rec.a, s), "event");
-        }
-        MDX_CUDA(launch_plate(P, p->n_cta, smem, s), "plate kernel");
-        if (p->profiling) {
-            MDX_CUDA(cudaEventRecord(rec.b, s), "event");
-            p->recs.push_back(rec);
-        }
+int run_plate(mdx_plan *p, PlateParams &P, cudaStream_t s) {
+    if (!p->any_plate) return MDX_OK;
+    MDX_CUDA(cudaMemsetAsync(p->d_counters, 0, p->n_inst * sizeof(unsigned), s), "memset");
+    MDX_CUDA(cudaMemsetAsync(p->d_abort, 0, sizeof(int), s), "memset");
+    const size_t smem = (P.mode == MODE_FUSED) ? p->smem_fused
+                        : (P.mode == MODE_REVERSE) ? p->smem_rev : p->smem_fwd;
+    mdx_plan::Rec rec{};
+    if (p->profiling) {
+        rec.which = P.mode;
+        rec.bytes = (double)P.steps * p->H_bytes_per_step;
+        MDX_CUDA(cudaEventCreate(&rec.a), "event");
+        MDX_CUDA(cudaEventCreate(&rec.b), "event");
+        MDX_CUDA(cudaEventRecord(rec.a, s), "event");
+    }
+    MDX_CUDA(launch_plate(P, p->n_cta, smem, s), "plate kernel");
+    if (p->profiling) {
+        MDX_CUDA(cudaEventRecord(rec.b, s), "event");
+        p->recs.push_back(rec);
     }
     return MDX_OK;
+}
+
+int run_segment(mdx_plan *p, PlateParams &P, TensionParams &T, cudaStream_t s) {
+    if (!p->tension.empty()) MDX_CUDA(launch_tension(T, p->tension_max_n, s), "tension kernel");
+    return run_plate(p, P, s);
 }
 
 }  // namespace
@@ -931,6 +1046,7 @@ namespace {
 
 struct GradWork {
     float *seg_q, *seg_v, *adj, *gacc, *kacc, *tacc, *seg_w, *xe;
+    float *seg_q2, *seg_v2;   // second segment buffer of the fused sweep (or null)
     double *dir_acc;
     size_t bytes;
 };
@@ -948,6 +1064,8 @@ GradWork grad_layout(const mdx_plan *p, int K, void *base) {
     };
     w.seg_q = take((size_t)(K + 1) * TM);
     w.seg_v = take((size_t)(K + 1) * TM);
+    w.seg_q2 = p->fuse ? take((size_t)(K + 1) * TM) : nullptr;
+    w.seg_v2 = p->fuse ? take((size_t)(K + 1) * TM) : nullptr;
     w.adj = take(AD_N * TM);
     w.gacc = take(2 * GA_N * TM);
     w.kacc = take(2 * TK);
@@ -993,25 +1111,32 @@ extern "C" int mdx_grad(mdx_plan *p, const float *exc, const double *q0, const d
                                  p->total_modes, 0, s),
              "init adjoint");
     const int nseg = (steps + K - 1) / K;
-    for (int sg = nseg - 1; sg >= 0; --sg) {
-        const int n0 = sg * K;
-        const int L = std::min(K, steps - n0);
-        // recompute the segment from its checkpoint, storing every state
-        PlateParams P = base_plate(p, MODE_RECOMPUTE, L, n0, steps);
-        TensionParams T = base_tension(p, MODE_RECOMPUTE, L, n0, steps);
+    float *const ckf = const_cast<float *>(static_cast<const float *>(ckpt));
+    auto seg_len = [&](int sg) { return std::min(K, steps - sg * K); };
+    // recompute segment sg from its checkpoint into (sq, sv), every state stored
+    auto recompute = [&](int sg, float *sq, float *sv, bool plates, bool tension) -> int {
+        PlateParams P = base_plate(p, MODE_RECOMPUTE, seg_len(sg), sg * K, steps);
+        TensionParams T = base_tension(p, MODE_RECOMPUTE, seg_len(sg), sg * K, steps);
         P.exc = T.exc = exc;
         P.ckpt_K = T.ckpt_K = K;
-        P.ckpt = T.ckpt = const_cast<float *>(static_cast<const float *>(ckpt));
-        P.seg_q = T.seg_q = w.seg_q;
-        P.seg_v = T.seg_v = w.seg_v;
+        P.ckpt = T.ckpt = ckf;
+        P.seg_q = T.seg_q = sq;
+        P.seg_v = T.seg_v = sv;
         P.status = T.status = status;
-        int rc = run_segment(p, P, T, s);
-        if (rc) return rc;
-        // adjoint sweep over the segment
-        P.mode = T.mode = MODE_REVERSE;
-        P.ring_stages = p->ring_rev;
-        P.u_slots = p->u_slots_rev;
-        P.u_floats = p->u_floats_rev;
+        if (tension && !p->tension.empty())
+            MDX_CUDA(launch_tension(T, p->tension_max_n, s), "tension kernel");
+        return plates ? run_plate(p, P, s) : MDX_OK;
+    };
+    auto reverse_params = [&](int sg, int mode, float *sq, float *sv, PlateParams &P,
+                              TensionParams &T) {
+        P = base_plate(p, mode, seg_len(sg), sg * K, steps);
+        T = base_tension(p, MODE_REVERSE, seg_len(sg), sg * K, steps);
+        P.exc = T.exc = exc;
+        P.ckpt_K = T.ckpt_K = K;
+        P.ckpt = T.ckpt = ckf;
+        P.seg_q = T.seg_q = sq;
+        P.seg_v = T.seg_v = sv;
+        P.status = T.status = status;
         P.ybar = T.ybar = d_audio;
         P.adj = T.adj = w.adj;
         P.gacc = T.gacc = w.gacc;
@@ -1020,37 +1145,76 @@ extern "C" int mdx_grad(mdx_plan *p, const float *exc, const double *q0, const d
         P.xe = w.xe;
         P.total_k = p->total_k;
         T.tacc = w.tacc;
-        rc = run_segment(p, P, T, s);
-        if (rc) return rc;
-        if (p->n_dir_units > 0) {
-            DirParams D{};
-            D.inst = p->d_inst;
-            D.units = p->d_dir_units;
-            D.groups = p->parity ? p->d_dir_groups : nullptr;
-            D.n_groups = p->parity ? p->n_dir_groups : 0;
-            D.dH = p->d_dH;
-            D.perm = p->d_perm;
-            D.kappa = p->d_kappa;
-            D.seg_q = w.seg_q;
-            D.seg_w = w.seg_w;
-            D.xe = w.xe;
-            D.dir_acc = w.dir_acc;
-            D.steps = L;
-            D.total_modes = p->total_modes;
-            D.total_k = p->total_k;
-            mdx_plan::Rec rec{};
-            if (p->profiling) {
-                rec.which = 3;
-                MDX_CUDA(cudaEventCreate(&rec.a), "event");
-                MDX_CUDA(cudaEventCreate(&rec.b), "event");
-                MDX_CUDA(cudaEventRecord(rec.a, s), "event");
-            }
-            MDX_CUDA(launch_dir_contract(D, p->n_dir_units, s), "direction contraction");
-            if (p->profiling) {
-                MDX_CUDA(cudaEventRecord(rec.b, s), "event");
-                p->recs.push_back(rec);
-            }
+    };
+    // direction contraction of segment sg (reads its stored states)
+    auto direction = [&](int sg, const float *sq) -> int {
+        if (p->n_dir_units <= 0) return MDX_OK;
+        DirParams D{};
+        D.inst = p->d_inst;
+        D.units = p->d_dir_units;
+        D.groups = p->parity ? p->d_dir_groups : nullptr;
+        D.n_groups = p->parity ? p->n_dir_groups : 0;
+        D.dH = p->d_dH;
+        D.perm = p->d_perm;
+        D.kappa = p->d_kappa;
+        D.seg_q = sq;
+        D.seg_w = w.seg_w;
+        D.xe = w.xe;
+        D.dir_acc = w.dir_acc;
+        D.steps = seg_len(sg);
+        D.total_modes = p->total_modes;
+        D.total_k = p->total_k;
+        mdx_plan::Rec rec{};
+        if (p->profiling) {
+            rec.which = 3;
+            MDX_CUDA(cudaEventCreate(&rec.a), "event");
+            MDX_CUDA(cudaEventCreate(&rec.b), "event");
+            MDX_CUDA(cudaEventRecord(rec.a, s), "event");
         }
+        MDX_CUDA(launch_dir_contract(D, p->n_dir_units, s), "direction contraction");
+        if (p->profiling) {
+            MDX_CUDA(cudaEventRecord(rec.b, s), "event");
+            p->recs.push_back(rec);
+        }
+        return MDX_OK;
+    };
+    int rc;
+    if (!p->fuse || !p->any_plate) {
+        for (int sg = nseg - 1; sg >= 0; --sg) {
+            if ((rc = recompute(sg, w.seg_q, w.seg_v, true, true))) return rc;
+            PlateParams P;
+            TensionParams T;
+            reverse_params(sg, MODE_REVERSE, w.seg_q, w.seg_v, P, T);
+            if ((rc = run_segment(p, P, T, s))) return rc;
+            if ((rc = direction(sg, w.seg_q))) return rc;
+        }
+    } else {
+        // Fused sweep: the launch for segment sg runs its adjoint (reading
+        // buffer sg & 1) and, in the same pass over H per step, recomputes
+        // segment sg - 1 from its checkpoint into the other buffer.  H is
+        // streamed nseg + 1 times per gradient instead of 2 nseg times.
+        float *bq[2] = {w.seg_q, w.seg_q2}, *bv[2] = {w.seg_v, w.seg_v2};
+        if ((rc = recompute(nseg - 1, bq[(nseg - 1) & 1], bv[(nseg - 1) & 1], true, true))) return rc;
+        for (int sg = nseg - 1; sg >= 1; --sg) {
+            const int cur = sg & 1, prv = (sg - 1) & 1;
+            PlateParams P;
+            TensionParams T;
+            reverse_params(sg, MODE_FUSED, bq[cur], bv[cur], P, T);
+            P.steps = K;                      // segment sg - 1 is a full segment
+            P.rev_steps = seg_len(sg);
+            P.rec_begin = (sg - 1) * K;
+            P.rseg_q = bq[prv];
+            P.rseg_v = bv[prv];
+            if ((rc = recompute(sg - 1, bq[prv], bv[prv], false, true))) return rc;
+            if (!p->tension.empty()) MDX_CUDA(launch_tension(T, p->tension_max_n, s), "tension kernel");
+            if ((rc = run_plate(p, P, s))) return rc;
+            if ((rc = direction(sg, bq[cur]))) return rc;
+        }
+        PlateParams P;
+        TensionParams T;
+        reverse_params(0, MODE_REVERSE, bq[0], bv[0], P, T);
+        if ((rc = run_segment(p, P, T, s))) return rc;
+        if ((rc = direction(0, bq[0]))) return rc;
     }
     GradEpilogue g{};
     g.inst = p->d_inst;
@@ -1130,14 +1294,14 @@ extern "C" int mdx_plan_reset_stats(mdx_plan *p) {
         cudaEventDestroy(r.b);
     }
     p->recs.clear();
-    for (int i = 0; i < 4; ++i) p->stat_launch[i] = 0, p->stat_ms[i] = 0, p->stat_bytes[i] = 0;
+    for (int i = 0; i < 5; ++i) p->stat_launch[i] = 0, p->stat_ms[i] = 0, p->stat_bytes[i] = 0;
     return MDX_OK;
 }
 
 extern "C" int mdx_plan_kernel_stats(mdx_plan *p, int which, long *launches, double *ms,
                                      double *bytes) {
     if (!p) return fail(MDX_ERR_ARG, "plan is NULL");
-    if (which < 0 || which > 3) return fail(MDX_ERR_ARG, "which must be 0..3");
+    if (which < 0 || which > 4) return fail(MDX_ERR_ARG, "which must be 0..4");
     for (auto &r : p->recs) {
         MDX_CUDA(cudaEventSynchronize(r.b), "event sync");
         float t = 0.f;
@@ -1163,6 +1327,16 @@ extern "C" int mdx_plan_configure(mdx_plan *p, int stage_bytes, int ring_stages)
     MDX_CUDA(cudaSetDevice(p->device), "cudaSetDevice");
     return configure_tiles(p, stage_bytes, ring_stages);
 }
+
+extern "C" int mdx_plan_set_l2_keep(mdx_plan *p, double fraction) {
+    if (!p) return fail(MDX_ERR_ARG, "plan is NULL");
+    if (!(fraction <= 1.0) && !(fraction < 0.0)) return fail(MDX_ERR_ARG, "fraction must be <= 1");
+    p->l2_keep_req = fraction < 0.0 ? -1.0 : fraction;
+    update_l2_keep(p);
+    return MDX_OK;
+}
+
+extern "C" double mdx_plan_l2_keep(const mdx_plan *p) { return p ? (double)p->l2_keep : 0.0; }
 
 extern "C" int mdx_plan_tiles(const mdx_plan *p, int *stage_bytes, int *ring_fwd, int *ring_rev,
                               int *ctas) {

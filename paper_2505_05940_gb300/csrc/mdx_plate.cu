@@ -82,6 +82,26 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+// Same copy with an L2 eviction-priority hint (a policy from createpolicy).
+__device__ __forceinline__ void bulk_g2s_hint(void *dst, const void *src, uint32_t bytes,
+                                              uint64_t *bar, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+        "[%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+
+// L2 policy: a `fraction` of the addresses (chosen by the hardware's address
+// hash) is kept with evict_last priority, the rest is marked evict_first.
+__device__ __forceinline__ uint64_t l2_keep_policy(float fraction) {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.L2::evict_first.b64 %0, %1;"
+                 : "=l"(pol)
+                 : "f"(fraction));
+    return pol;
+}
+
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -137,7 +157,8 @@ __device__ __forceinline__ void fma4(float4 &acc, const float4 &h, float x) {
     acc.w = fmaf(h.w, x, acc.w);
 }
 
-// R: right-hand sides of the H pass (1: forward / recompute; 2: reverse).
+// R: right-hand sides of the H pass (1: forward / recompute; 2: reverse;
+// 3: fused reverse + recompute of the previous segment, class layout only).
 // PAR: coupling stored in symmetry-class chunks (see ParityChunk).
 template <int R, bool PAR>
 __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams P) {
@@ -168,7 +189,11 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
     S.state = reinterpret_cast<float *>(p);
 
     volatile int *gabort = P.abort_flag;
-    const bool reverse = (P.mode == MODE_REVERSE);
+    constexpr bool FUSED = (R == 3);
+    static_assert(!FUSED || PAR, "the fused sweep exists for the class layout only");
+    const bool reverse = FUSED || (P.mode == MODE_REVERSE);
+    // reverse steps of this launch (the fused sweep may run more recompute steps)
+    const int rsteps = FUSED ? P.rev_steps : P.steps;
 
     if (tid == 0) {
         for (int s = 0; s < RING; ++s) {
@@ -185,7 +210,20 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
     if (tid >= kPlateThreads) {
         if (tid == kPlateThreads) {
             long long seq = 0;
+            int slot = 0;              // seq % RING and the parity of seq / RING, kept
+            uint32_t ring_ph = 0;      // incrementally (no 64-bit division per stage)
             bool ok = true;
+            // The coupling data is re-read every step: when it (nearly) fits in
+            // L2, keeping a fraction of it resident saves that share of the
+            // HBM traffic of every later step.
+            const bool hint = P.l2_keep > 0.f;
+            const uint64_t pol = hint ? l2_keep_policy(fminf(P.l2_keep, 1.f)) : 0ull;
+            auto copy = [&](void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+                if (hint)
+                    bulk_g2s_hint(dst, src, bytes, bar, pol);
+                else
+                    bulk_g2s(dst, src, bytes, bar);
+            };
             for (int it = 0; it < P.steps && ok; ++it) {
                 for (int ii = it0; ii < it1 && ok; ++ii) {
                     const PlateItem item = P.items[ii];
@@ -206,18 +244,22 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                                     const int rps = max(1, stage_floats / L);
                                     for (int p0 = 0; p0 < na; p0 += rps) {
                                         const int nr = min(rps, na - p0);
-                                        const int s = (int)(seq % RING);
-                                        const uint32_t ph = (uint32_t)((seq / RING) & 1);
+                                        const int s = slot;
+                                        const uint32_t ph = ring_ph;
                                         if (!mbar_wait(&S.empty[s], ph ^ 1u, P.wait_limit, gabort)) {
                                             ok = false;
                                             break;
                                         }
                                         const uint32_t bytes = (uint32_t)nr * L * 4u;
                                         mbar_arrive_expect_tx(&S.full[s], bytes);
-                                        bulk_g2s(S.ring + (size_t)s * stage_floats, base + cur, bytes,
-                                                 &S.full[s]);
+                                        copy(S.ring + (size_t)s * stage_floats, base + cur, bytes,
+                                             &S.full[s]);
                                         cur += (long long)nr * L;
                                         ++seq;
+                                        if (++slot == RING) {
+                                            slot = 0;
+                                            ring_ph ^= 1u;
+                                        }
                                     }
                                 }
                             }
@@ -229,17 +271,21 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                                                 (long long)k * d.N * d.Npad;
                             for (int p0 = 0; p0 < d.N; p0 += rows_per_stage) {
                                 const int nr = min(rows_per_stage, d.N - p0);
-                                const int s = (int)(seq % RING);
-                                const uint32_t ph = (uint32_t)((seq / RING) & 1);
+                                const int s = slot;
+                                const uint32_t ph = ring_ph;
                                 if (!mbar_wait(&S.empty[s], ph ^ 1u, P.wait_limit, gabort)) {
                                     ok = false;
                                     break;
                                 }
                                 const uint32_t bytes = (uint32_t)nr * d.Npad * 4u;
                                 mbar_arrive_expect_tx(&S.full[s], bytes);
-                                bulk_g2s(S.ring + (size_t)s * stage_floats,
-                                         base + (long long)p0 * d.Npad, bytes, &S.full[s]);
+                                copy(S.ring + (size_t)s * stage_floats,
+                                     base + (long long)p0 * d.Npad, bytes, &S.full[s]);
                                 ++seq;
+                                if (++slot == RING) {
+                                    slot = 0;
+                                    ring_ph ^= 1u;
+                                }
                             }
                         }
                     }
@@ -257,7 +303,8 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
     // ======================================================= consumer warps
     const int warp = tid >> 5, lane = tid & 31;
     const long long TM = P.total_modes;
-    long long seq = 0;         // stages consumed
+    int slot = 0;              // ring slot of the next stage to consume
+    uint32_t ring_ph = 0;      // its mbarrier phase parity
     int chunk_parity = 0;
     int red2_parity = 0;
     // A failed wait is recorded in fail / S.misc[1] but the thread keeps the
@@ -288,14 +335,22 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
             st[ST_QLO * d.Npad + s] = in ? src[stride + d.mode_off + s] : 0.f;
             st[ST_V * d.Npad + s] = in ? src[2 * stride + d.mode_off + s] : 0.f;
             st[ST_VLO * d.Npad + s] = (in && !reverse) ? src[3 * stride + d.mode_off + s] : 0.f;
+            if constexpr (FUSED) {
+                const float *ck = P.ckpt + (long long)(P.rec_begin / P.ckpt_K) * kStateArrays * TM;
+                st[ST_RQHI * d.Npad + s] = in ? ck[d.mode_off + s] : 0.f;
+                st[ST_RQLO * d.Npad + s] = in ? ck[TM + d.mode_off + s] : 0.f;
+                st[ST_RV * d.Npad + s] = in ? ck[2 * TM + d.mode_off + s] : 0.f;
+                st[ST_RVLO * d.Npad + s] = in ? ck[3 * TM + d.mode_off + s] : 0.f;
+            }
         }
     }
     consumer_bar();
 
     for (int it = 0; it < P.steps; ++it) {
         // global step index: forward counts up, reverse counts down
-        const int t_loc = reverse ? (P.steps - 1 - it) : it;
+        const int t_loc = reverse ? (rsteps - 1 - it) : it;
         const int n = P.n_begin + t_loc;
+        const bool rev_on = it < rsteps;   // false only in the tail of a fused launch
 
         // -------- pre-pass: right-hand sides, checkpoints, stored states
         for (int ii = it0; ii < it1; ++ii) {
@@ -322,13 +377,21 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                     }
                     st[ST_FLOC * Np + s] = 0.f;
                 } else {
-                    const float qn = in ? P.seg_q[(long long)t_loc * TM + m] : 0.f;
-                    const float wv = in ? P.coef.r[m] * st[ST_QHI * Np + s] : 0.f;
+                    const bool live = in && rev_on;
+                    const float qn = live ? P.seg_q[(long long)t_loc * TM + m] : 0.f;
+                    const float wv = live ? P.coef.r[m] * st[ST_QHI * Np + s] : 0.f;
                     st[ST_SRC0 * Np + s] = qn;
                     st[ST_SRC1 * Np + s] = wv;
-                    if (in && item.owner && P.seg_w) P.seg_w[(long long)t_loc * TM + m] = wv;
+                    if (live && item.owner && P.seg_w) P.seg_w[(long long)t_loc * TM + m] = wv;
                     st[ST_FLOC * Np + s] = 0.f;
                     st[ST_FLOC2 * Np + s] = 0.f;
+                    if constexpr (FUSED) {
+                        if (in && item.owner) {
+                            P.rseg_q[(long long)it * TM + m] = st[ST_RQHI * Np + s];
+                            P.rseg_v[(long long)it * TM + m] = st[ST_RV * Np + s];
+                        }
+                        st[ST_RFLOC * Np + s] = 0.f;
+                    }
                 }
             }
         }
@@ -345,6 +408,7 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                     const int su = P.perm[d.perm_off + mp];
                     st[ST_QP * Np + mp] = q[su];
                     if (reverse) st[ST_WP * Np + mp] = st[ST_SRC1 * Np + su];
+                    if constexpr (FUSED) st[ST_RQP * Np + mp] = st[ST_RQHI * Np + su];
                 }
             }
             consumer_bar();
@@ -370,8 +434,11 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
             const float *src1 = st + ST_SRC1 * Np;
             const int spt = (Np + kPlateThreads - 1) / kPlateThreads;
             if constexpr (PAR) {
+                // u slots per stress mode: H q, H w (reverse), H q' (fused recompute)
+                constexpr int US = FUSED ? 3 : 2;
                 const float *qp = st + ST_QP * Np;
                 const float *wp = st + ST_WP * Np;
+                const float *rp = st + (FUSED ? ST_RQP : ST_QP) * Np;
                 float *red = S.red;
                 for (int ci = item.chunk0; ci < item.chunk1; ++ci) {
                     const ParityChunk ch = P.chunks[ci];
@@ -379,93 +446,127 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                     const int tpk = par_tpk(mc);
                     const int kl = tid / tpk, c4 = tid - (tid / tpk) * tpk;
                     const bool kact = kl < mc;
-                    float dsum[4] = {0.f, 0.f, 0.f, 0.f};
-                    for (int mat = 0; mat < nmat; ++mat) {
-                        for (int a = 0; a < 4; ++a) {
-                            const int bcl = a ^ ch.c;
-                            const int na = pick4(d.ncls, a), nbc = pick4(d.ncls, bcl);
-                            if (na == 0 || nbc == 0) continue;
-                            const int oa = pick4(d.ocls, a), ob = pick4(d.ocls, bcl);
-                            const int nb4 = (nbc + 3) & ~3, nq = nb4 >> 2;
-                            const int L = mc * nb4;
-                            const int rps = max(1, stage_floats / L);
-                            // each thread owns column quads qi0 = c4 and qi1 = c4 + tpk
-                            const int qi0 = c4, qi1 = c4 + tpk;
-                            const bool h0 = kact && qi0 < nq, h1 = kact && qi1 < nq;
-                            const bool two = (R > 1) && (mat == 0);
-                            float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
-                            for (int p0 = 0; p0 < na; p0 += rps) {
-                                const int nr = min(rps, na - p0);
-                                const int s = (int)(seq % RING);
-                                const uint32_t ph = (uint32_t)((seq / RING) & 1);
-                                if (!fail && !mbar_wait(&S.full[s], ph, P.wait_limit, gabort)) {
-                                    fail = true;
-                                    *reinterpret_cast<volatile int *>(&S.misc[1]) = 1;
-                                    atomicExch((int *)gabort, 1);
-                                }
-                                if (h0) {
-                                    const float *row = S.ring + (size_t)s * stage_floats + kl * nb4 + 4 * qi0;
-                                    const float *xs = qp + oa + p0;
-                                    const float *ys = wp + oa + p0;
-                                    if (h1) {
-#pragma unroll 2
-                                        for (int r = 0; r < nr; ++r) {
-                                            const float4 hA = *reinterpret_cast<const float4 *>(row + (size_t)r * L);
-                                            const float4 hB = *reinterpret_cast<const float4 *>(row + (size_t)r * L + 4 * tpk);
-                                            const float x = xs[r];
-                                            fma4(a0, hA, x);
-                                            fma4(b0, hB, x);
-                                            if (two) {
-                                                const float y = ys[r];
-                                                fma4(a1, hA, y);
-                                                fma4(b1, hB, y);
-                                            }
-                                        }
-                                    } else {
-#pragma unroll 4
-                                        for (int r = 0; r < nr; ++r) {
-                                            const float4 hA = *reinterpret_cast<const float4 *>(row + (size_t)r * L);
-                                            fma4(a0, hA, xs[r]);
-                                            if (two) fma4(a1, hA, ys[r]);
-                                        }
-                                    }
-                                }
-                                __syncwarp();
-                                if (lane == 0) mbar_arrive(&S.empty[s]);
-                                ++seq;
+                    float dsum[3] = {0.f, 0.f, 0.f};
+                    for (int a = 0; a < 4; ++a) {
+                        const int bcl = a ^ ch.c;
+                        const int na = pick4(d.ncls, a), nbc = pick4(d.ncls, bcl);
+                        if (na == 0 || nbc == 0) continue;
+                        const int oa = pick4(d.ocls, a), ob = pick4(d.ocls, bcl);
+                        const int nb4 = (nbc + 3) & ~3, nq = nb4 >> 2;
+                        const int L = mc * nb4;
+                        const int rps = max(1, stage_floats / L);
+                        // each thread owns column quads qi0 = c4 and qi1 = c4 + tpk
+                        const int qi0 = c4, qi1 = c4 + tpk;
+                        const bool h0 = kact && qi0 < nq, h1 = kact && qi1 < nq;
+                        constexpr bool two = R > 1;
+                        float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
+                        float4 c0 = a0, c1 = a0;
+                        for (int p0 = 0; p0 < na; p0 += rps) {
+                            const int nr = min(rps, na - p0);
+                            const int s = slot;
+                            const uint32_t ph = ring_ph;
+                            if (!fail && !mbar_wait(&S.full[s], ph, P.wait_limit, gabort)) {
+                                fail = true;
+                                *reinterpret_cast<volatile int *>(&S.misc[1]) = 1;
+                                atomicExch((int *)gabort, 1);
                             }
-                            // this super-block completes u^k (and z^k, t^k) on the columns of class b
-#pragma unroll
-                            for (int half = 0; half < 2; ++half) {
-                                const bool has = half == 0 ? h0 : h1;
-                                if (!has) continue;
-                                const int qi = half == 0 ? qi0 : qi1;
-                                const float4 va = half == 0 ? a0 : b0;
-                                const float4 vb = half == 0 ? a1 : b1;
-#pragma unroll
-                                for (int e = 0; e < 4; ++e) {
-                                    const int cs = 4 * qi + e;
-                                    if (cs >= nbc) break;
-                                    const int mp = ob + cs;
-                                    const float v0 = comp4(va, e);
-                                    if (mat == 0) {
-                                        S.U[((size_t)kl * 2 + 0) * P.npad_max + mp] = v0;
-                                        dsum[0] = fmaf(qp[mp], v0, dsum[0]);
-                                        if (R > 1) {
-                                            S.U[((size_t)kl * 2 + 1) * P.npad_max + mp] = comp4(vb, e);
-                                            dsum[1] = fmaf(wp[mp], v0, dsum[1]);
+                            if (h0) {
+                                const float *row = S.ring + (size_t)s * stage_floats + kl * nb4 + 4 * qi0;
+                                const float *xs = qp + oa + p0;
+                                const float *ys = wp + oa + p0;
+                                const float *zs = rp + oa + p0;
+                                if (h1) {
+#pragma unroll 2
+                                    for (int r = 0; r < nr; ++r) {
+                                        const float4 hA = *reinterpret_cast<const float4 *>(row + (size_t)r * L);
+                                        const float4 hB = *reinterpret_cast<const float4 *>(row + (size_t)r * L + 4 * tpk);
+                                        const float x = xs[r];
+                                        fma4(a0, hA, x);
+                                        fma4(b0, hB, x);
+                                        if (two) {
+                                            const float y = ys[r];
+                                            fma4(a1, hA, y);
+                                            fma4(b1, hB, y);
                                         }
-                                    } else {
-                                        dsum[2] = fmaf(qp[mp], v0, dsum[2]);
-                                        dsum[3] = fmaf(wp[mp], v0, dsum[3]);
+                                        if constexpr (FUSED) {
+                                            const float z = zs[r];
+                                            fma4(c0, hA, z);
+                                            fma4(c1, hB, z);
+                                        }
                                     }
+                                } else {
+                                    // one column quad: two independent chains over
+                                    // alternate rows (odd rows accumulate in the
+                                    // second quad's registers, folded in below)
+                                    int r = 0;
+#pragma unroll 2
+                                    for (; r + 1 < nr; r += 2) {
+                                        const float4 hA = *reinterpret_cast<const float4 *>(row + (size_t)r * L);
+                                        const float4 hB = *reinterpret_cast<const float4 *>(row + (size_t)(r + 1) * L);
+                                        fma4(a0, hA, xs[r]);
+                                        fma4(b0, hB, xs[r + 1]);
+                                        if (two) {
+                                            fma4(a1, hA, ys[r]);
+                                            fma4(b1, hB, ys[r + 1]);
+                                        }
+                                        if constexpr (FUSED) {
+                                            fma4(c0, hA, zs[r]);
+                                            fma4(c1, hB, zs[r + 1]);
+                                        }
+                                    }
+                                    if (r < nr) {
+                                        const float4 hA = *reinterpret_cast<const float4 *>(row + (size_t)r * L);
+                                        fma4(a0, hA, xs[r]);
+                                        if (two) fma4(a1, hA, ys[r]);
+                                        if constexpr (FUSED) fma4(c0, hA, zs[r]);
+                                    }
+                                }
+                            }
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&S.empty[s]);
+                            if (++slot == RING) {
+                                slot = 0;
+                                ring_ph ^= 1u;
+                            }
+                        }
+                        if (h0 && !h1) {
+                            a0 = make_float4(a0.x + b0.x, a0.y + b0.y, a0.z + b0.z, a0.w + b0.w);
+                            a1 = make_float4(a1.x + b1.x, a1.y + b1.y, a1.z + b1.z, a1.w + b1.w);
+                            c0 = make_float4(c0.x + c1.x, c0.y + c1.y, c0.z + c1.z, c0.w + c1.w);
+                        }
+                        // this super-block completes u^k (and z^k, u'^k) on the columns of class b
+#pragma unroll
+                        for (int half = 0; half < 2; ++half) {
+                            const bool has = half == 0 ? h0 : h1;
+                            if (!has) continue;
+                            const int qi = half == 0 ? qi0 : qi1;
+                            const float4 va = half == 0 ? a0 : b0;
+                            const float4 vb = half == 0 ? a1 : b1;
+                            const float4 vc = half == 0 ? c0 : c1;
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const int cs = 4 * qi + e;
+                                if (cs >= nbc) break;
+                                const int mp = ob + cs;
+                                const float v0 = comp4(va, e);
+                                S.U[((size_t)kl * US + 0) * P.npad_max + mp] = v0;
+                                dsum[0] = fmaf(qp[mp], v0, dsum[0]);
+                                if (R > 1) {
+                                    S.U[((size_t)kl * US + 1) * P.npad_max + mp] = comp4(vb, e);
+                                    dsum[1] = fmaf(wp[mp], v0, dsum[1]);
+                                }
+                                if constexpr (FUSED) {
+                                    const float v2 = comp4(vc, e);
+                                    S.U[((size_t)kl * US + 2) * P.npad_max + mp] = v2;
+                                    dsum[2] = fmaf(rp[mp], v2, dsum[2]);
                                 }
                             }
                         }
                     }
                     // dot products of each stress mode: reduce over its tpk lanes
+                    constexpr int ND = FUSED ? 3 : (R > 1 ? 2 : 1);
 #pragma unroll
-                    for (int dd = 0; dd < 4; ++dd) {
+                    for (int dd = 0; dd < ND; ++dd) {
                         float v = dsum[dd];
                         for (int o = tpk >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                         if (kact && c4 == 0) red[kl * 4 + dd] = v;
@@ -474,26 +575,30 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                     // forces, per mode in class order (each thread owns distinct modes)
                     for (int mp = tid; mp < d.N; mp += kPlateThreads) {
                         const int su = P.perm[d.perm_off + mp];
-                        float fa = 0.f, fb = 0.f;
+                        float fa = 0.f, fb = 0.f, fr = 0.f;
                         for (int q = 0; q < mc; ++q) {
                             const float kap = P.kappa[d.k_off + ch.kl0 + q];
                             const float eta = red[q * 4 + 0];
-                            const float u = S.U[((size_t)q * 2 + 0) * P.npad_max + mp];
+                            const float u = S.U[((size_t)q * US + 0) * P.npad_max + mp];
                             if (!reverse) {
                                 fa = fmaf(kap * eta, u, fa);
                             } else {
-                                const float z = S.U[((size_t)q * 2 + 1) * P.npad_max + mp];
+                                const float z = S.U[((size_t)q * US + 1) * P.npad_max + mp];
                                 fb = fmaf(kap * eta, u, fb);
                                 fa = fmaf(kap, fmaf(2.f * red[q * 4 + 1], u, eta * z), fa);
+                            }
+                            if constexpr (FUSED) {
+                                const float u2 = S.U[((size_t)q * US + 2) * P.npad_max + mp];
+                                fr = fmaf(kap * red[q * 4 + 2], u2, fr);
                             }
                         }
                         st[ST_FLOC * Np + su] += fa;
                         if (reverse) st[ST_FLOC2 * Np + su] += fb;
+                        if constexpr (FUSED) st[ST_RFLOC * Np + su] += fr;
                     }
-                    if (reverse && tid == 0) {
+                    if (reverse && rev_on && tid == 0) {
                         for (int q = 0; q < mc; ++q) {
                             const long long kk = d.k_off + ch.kl0 + q;
-                            const float kap = P.kappa[kk];
                             const float eta = red[q * 4 + 0], xi = red[q * 4 + 1];
                             float *ka = P.kacc + 2 * kk;
                             float s0 = ka[0], c0 = ka[1];
@@ -504,7 +609,6 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                                 P.xe[((long long)t_loc * 2 + 0) * P.total_k + kk] = xi;
                                 P.xe[((long long)t_loc * 2 + 1) * P.total_k + kk] = eta;
                             }
-                            (void)kap;
                         }
                     }
                     consumer_bar();
@@ -519,8 +623,8 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                         float4 a1 = make_float4(0.f, 0.f, 0.f, 0.f);
                         for (int p0 = 0; p0 < d.N; p0 += rows_per_stage) {
                             const int nr = min(rows_per_stage, d.N - p0);
-                            const int s = (int)(seq % RING);
-                            const uint32_t ph = (uint32_t)((seq / RING) & 1);
+                            const int s = slot;
+                            const uint32_t ph = ring_ph;
                             if (!fail && !mbar_wait(&S.full[s], ph, P.wait_limit, gabort)) {
                                 fail = true;
                                 *reinterpret_cast<volatile int *>(&S.misc[1]) = 1;
@@ -560,7 +664,10 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                             }
                             __syncwarp();
                             if (lane == 0) mbar_arrive(&S.empty[s]);
-                            ++seq;
+                            if (++slot == RING) {
+                                slot = 0;
+                                ring_ph ^= 1u;
+                            }
                         }
                         if (active) {
                             // slot 0: H q, slot 1: H w (reverse), slot 2: dH q (direction)
@@ -670,6 +777,7 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                 for (int s = tid; s < Np; s += kPlateThreads) {
                     P.part[slot_base + s] = st[ST_FLOC * Np + s];
                     if (reverse) P.part[slot_base + Np + s] = st[ST_FLOC2 * Np + s];
+                    if constexpr (FUSED) P.part[slot_base + 2 * Np + s] = st[ST_RFLOC * Np + s];
                 }
                 consumer_bar();
                 if (tid == 0 && !((P.debug_flags & 1) && item.slot == 1)) {
@@ -702,21 +810,25 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                 }
                 consumer_bar();
             }
-            const float e = P.exc ? P.exc[(long long)item.inst * P.total_steps + n] : 0.f;
+            const float e = (P.exc && rev_on) ? P.exc[(long long)item.inst * P.total_steps + n] : 0.f;
+            const float e_rec =
+                (FUSED && P.exc) ? P.exc[(long long)item.inst * P.total_steps + P.rec_begin + it] : 0.f;
             float yp = 0.f;
             for (int s = tid; s < d.N; s += kPlateThreads) {
                 const long long m = d.mode_off + s;
-                float fA, fB = 0.f;
+                float fA, fB = 0.f, fR = 0.f;
                 if (d.n_contrib > 1) {
                     const long long base = (long long)(it & 1) * P.part_stride + d.part_off;
                     fA = 0.f;
                     for (int c = 0; c < d.n_contrib; ++c) {
                         fA += ld_cg(P.part + base + (long long)c * 3 * Np + s);
                         if (reverse) fB += ld_cg(P.part + base + (long long)c * 3 * Np + Np + s);
+                        if constexpr (FUSED) fR += ld_cg(P.part + base + (long long)c * 3 * Np + 2 * Np + s);
                     }
                 } else {
                     fA = st[ST_FLOC * Np + s];
                     if (reverse) fB = st[ST_FLOC2 * Np + s];
+                    if constexpr (FUSED) fR = st[ST_RFLOC * Np + s];
                 }
                 const float eps = P.coef.eps[m], rw2 = P.coef.rw2[m], r = P.coef.r[m];
                 const float rw2l = P.coef.rw2lo[m];
@@ -726,7 +838,7 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                 if (!reverse) {
                     sv_step(x0, x1, x2, x3, eps, rw2, rw2l, r, fmaf(b, e, -fA));
                     yp = fmaf(c, x0, yp);
-                } else {
+                } else if (rev_on) {
                     // fA = J w (summed), fB = fnl(q^n)
                     if (item.owner) {
                         const float a = x0;
@@ -757,6 +869,16 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                 st[ST_QLO * Np + s] = x1;
                 st[ST_V * Np + s] = x2;
                 st[ST_VLO * Np + s] = x3;
+                if constexpr (FUSED) {
+                    // recompute of the previous segment: the forward update at q'
+                    float y0 = st[ST_RQHI * Np + s], y1 = st[ST_RQLO * Np + s];
+                    float y2 = st[ST_RV * Np + s], y3 = st[ST_RVLO * Np + s];
+                    sv_step(y0, y1, y2, y3, eps, rw2, rw2l, r, fmaf(b, e_rec, -fR));
+                    st[ST_RQHI * Np + s] = y0;
+                    st[ST_RQLO * Np + s] = y1;
+                    st[ST_RV * Np + s] = y2;
+                    st[ST_RVLO * Np + s] = y3;
+                }
             }
             if (!reverse) {
                 // pickup y^n (owner) ; reduction buffer alternates so one barrier suffices
@@ -808,6 +930,10 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                     P.adj[m] = st[ST_QHI * Np + s];
                     P.adj[TM + m] = st[ST_QLO * Np + s];
                     P.adj[2 * TM + m] = st[ST_V * Np + s];
+                    if constexpr (FUSED) {
+                        P.rseg_q[(long long)P.steps * TM + m] = st[ST_RQHI * Np + s];
+                        P.rseg_v[(long long)P.steps * TM + m] = st[ST_RV * Np + s];
+                    }
                 }
             }
         }
@@ -851,6 +977,7 @@ cudaError_t plate_set_smem_limit(size_t smem) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(plate_kernel<2, false>, A, (int)smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(plate_kernel<1, true>, A, (int)smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(plate_kernel<2, true>, A, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(plate_kernel<3, true>, A, (int)smem);
     return e;
 }
 
@@ -870,9 +997,11 @@ cudaError_t launch_plate(const PlateParams &p, int grid, size_t smem, cudaStream
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (p.parity) {
+        if (p.mode == MODE_FUSED) return cudaLaunchKernelEx(&cfg, plate_kernel<3, true>, p);
         if (p.mode == MODE_REVERSE) return cudaLaunchKernelEx(&cfg, plate_kernel<2, true>, p);
         return cudaLaunchKernelEx(&cfg, plate_kernel<1, true>, p);
     }
+    if (p.mode == MODE_FUSED) return cudaErrorInvalidValue;   // class layout only
     if (p.mode == MODE_REVERSE) return cudaLaunchKernelEx(&cfg, plate_kernel<2, false>, p);
     return cudaLaunchKernelEx(&cfg, plate_kernel<1, false>, p);
 }
