@@ -15,6 +15,14 @@ value = plate mode-steps per second = n_gpus * 64 * 200 * 22050 / step time.
 
   python bench.py [--gpus N --steps K --warmup W]      # this library
   python bench.py --impl reference                     # FP64 CPU oracle on host cores
+
+Secondary workloads (forward only, one JSON line each, not the headline):
+  --workload batched      512 ragged plates and membranes, N_phi log-uniform in
+                          [20, 400], aspects on 8 shared values (per-instance
+                          copies of the coupling data, 22 050 steps); compared
+                          with one instance per launch on a seeded subset
+  --workload string40     one 40-mode nonlinear string, 48 000 steps at 48 kHz
+  --workload plate100x30  one 100 x 30 steel plate, 44 100 steps
 """
 from __future__ import annotations
 
@@ -51,6 +59,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workers", type=int, default=0)
+    ap.add_argument("--workload", default="adjoint",
+                    choices=["adjoint", "batched", "string40", "plate100x30"])
     return ap.parse_args()
 
 
@@ -207,12 +217,107 @@ def reference_arm(a):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------- secondary workloads
+
+def _group_bank(args):
+    aspect, n_phi, n_psi = args
+    from paper_2505_05940_gb300 import proposal
+    return proposal._aspect_bank([aspect], n_phi=n_phi, n_psi=n_psi)
+
+
+def forward_workload(a):
+    """Forward-only throughput of the batched and single-instance workloads."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    from paper_2505_05940_gb300 import physics, proposal, workloads as W
+    if a.workload == "batched":
+        wl = W.batched_ragged(seed=0)
+        aspects = sorted({float(i.aspect) for i in wl.instances if i.kind == "plate"})
+        workers = a.workers or max(1, min(len(aspects), os.cpu_count() or 1))
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            banks = list(ex.map(_group_bank, [(x, 400, 100) for x in aspects]))
+        bank = {}
+        for b in banks:
+            bank.update(b)
+        cp = proposal._bank_coupling(bank)
+        prep = [physics.prepare(i, wl.fs, wl.steps, coupling=cp) for i in wl.instances]
+    else:
+        wl = W.string_40() if a.workload == "string40" else W.plate_100x30()
+        prep = [physics.prepare(i, wl.fs, wl.steps) for i in wl.instances]
+    import torch
+    from paper_2505_05940_gb300 import modal
+    sim = modal.Simulator(prep)
+    steps = wl.steps
+    modes = int(sum(len(p["omega2"]) for p in prep))
+    for _ in range(a.warmup):
+        sim.simulate(steps)
+    torch.cuda.synchronize()
+    sim.plan.set_profiling(True)
+    sim.plan.reset_stats()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        ev0.record(stream)
+        for _ in range(a.steps):
+            sim.simulate(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / a.steps
+    value = modes * steps / (ms * 1e-3)
+    n, pms, pby = sim.plan.kernel_stats(0)
+    peak, peak_kind = load_peaks()
+    line = {"metric": "mode-steps/s forward", "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+            "us_per_time_step": ms * 1e3 / steps, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "instances": len(prep), "total_modes": modes,
+                       "sim_steps": steps}, "clocks": clk.summary()}
+    if n:
+        ach = pby / (pms * 1e-3) / 1e9
+        line["plate_kernel"] = {"GB/s": ach, "frac_of_hbm": ach / peak,
+                                "peak_source": f"{peak_kind} hbm_gbs",
+                                "share_of_time": pms / (ms * a.steps)}
+    if a.workload == "batched":
+        # the plain form: one instance per plan and launch, on a seeded subset
+        rng = np.random.default_rng(1)
+        sub = sorted(rng.choice(len(prep), size=32, replace=False).tolist())
+        sub_steps = 2205
+        sims = [modal.Simulator([prep[i]]) for i in sub]
+        for s_ in sims:
+            s_.simulate(sub_steps)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for s_ in sims:
+            s_.simulate(sub_steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_one = ev0.elapsed_time(ev1)
+        sub_modes = sum(len(prep[i]["omega2"]) for i in sub)
+        one = sub_modes * sub_steps / (ms_one * 1e-3)
+        bsim = modal.Simulator([prep[i] for i in sub])
+        bsim.simulate(sub_steps)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        bsim.simulate(sub_steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        batched_sub = sub_modes * sub_steps / (ev0.elapsed_time(ev1) * 1e-3)
+        line["one_instance_per_launch"] = {
+            "subset": f"32 seeded instances, {sub_steps} steps", "value": one,
+            "same_subset_batched": batched_sub, "full_batch_over_one": value / one,
+            "subset_batched_over_one": batched_sub / one}
+    print(json.dumps(line), flush=True)
+
+
 # ----------------------------------------------------------------- main arm
 
 def main():
     a = parse()
     if a.impl == "reference":
         reference_arm(a)
+        return
+    if a.workload != "adjoint":
+        forward_workload(a)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

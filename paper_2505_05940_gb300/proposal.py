@@ -314,7 +314,8 @@ def fit(targets, init_lp, bank, fs=44100.0, steps=4410, iters=100, lr=0.05, K=10
     nonlinear scale are fitted.
 
     Returns dict(reached = first iteration at which every modal frequency is
-    within `tol` relative error (inf if never), lp = final estimates,
+    within `tol` relative error (inf if never), reached_all = first iteration
+    at which every fitted parameter is within `tol`, lp = final estimates,
     loss = final per-target loss, param_err = final |log error| per
     parameter)."""
     cp = _bank_coupling(bank)
@@ -335,6 +336,7 @@ def fit(targets, init_lp, bank, fs=44100.0, steps=4410, iters=100, lr=0.05, K=10
     m1 = np.zeros_like(lp)
     m2 = np.zeros_like(lp)
     reached = np.full(n, np.inf)
+    reached_all = np.full(n, np.inf)   # every fitted parameter within tol
     offs = sim.plan.mode_offset
     kap_off = np.cumsum([0] + [len(p["zeta4"]) if p["kind"] == "plate" and p.get("H") is not None
                                else 0 for p in preps])
@@ -342,6 +344,8 @@ def fit(targets, init_lp, bank, fs=44100.0, steps=4410, iters=100, lr=0.05, K=10
     for it in range(iters + 1):
         ok = _freq_error(preps, lp, true_lp) <= tol
         reached = np.where(ok & ~np.isfinite(reached), it, reached)
+        ok_all = np.all(np.where(mask, np.abs(np.exp(lp - true_lp) - 1.0) <= tol, True), axis=1)
+        reached_all = np.where(ok_all & ~np.isfinite(reached_all), it, reached_all)
         w2, gm, tau, kap = _coefficients(preps, lp)
         sim.plan.set_coefficients(omega2=w2, gamma=gm, tau=tau, kappa=kap)
         for tnsr in (sim.omega2, sim.gamma, sim.b, sim.c, sim.tau, sim.kappa, sim.q0, sim.qm1,
@@ -373,7 +377,7 @@ def fit(targets, init_lp, bank, fs=44100.0, steps=4410, iters=100, lr=0.05, K=10
         cur = lr * (0.01 + 0.99 * 0.5 * (1.0 + math.cos(math.pi * it / max(1, iters))))
         step = cur * (m1 / (1 - 0.9 ** (it + 1))) / (np.sqrt(m2 / (1 - 0.999 ** (it + 1))) + 1e-12)
         lp = _project(preps, lp - np.where(mask, step, 0.0), T)
-    return dict(reached=reached, lp=lp, true_lp=true_lp,
+    return dict(reached=reached, reached_all=reached_all, lp=lp, true_lp=true_lp,
                 loss=loss_i.detach().cpu().numpy() if loss_i is not None else None,
                 param_err=np.where(mask, np.abs(lp - true_lp), np.nan))
 
@@ -430,6 +434,7 @@ def study(n_train=200_000, n_test=1000, train_steps=11025, fit_steps=4410, iters
         r = fit(test.instances, init, bank, fs=test.fs, steps=fit_steps, iters=iters,
                 device=device)
         res[name] = dict(summarize(r["reached"]), seconds=time.perf_counter() - t0,
+                         all_params=summarize(r["reached_all"]),
                          final_loss_median=float(np.median(r["loss"])),
                          final_abs_log_err_median=np.nanmedian(r["param_err"], axis=0).tolist())
         log(f"{name}: {res[name]}")
@@ -446,9 +451,10 @@ if __name__ == "__main__":
     ap.add_argument("--test", type=int, default=1000)
     ap.add_argument("--iters", type=int, default=100)
     ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--fit-steps", type=int, default=4410)
     ap.add_argument("--out", default="")
     a = ap.parse_args()
-    out = study(a.train, a.test, iters=a.iters, epochs=a.epochs)
+    out = study(a.train, a.test, iters=a.iters, epochs=a.epochs, fit_steps=a.fit_steps)
     print(json.dumps(out))
     if a.out:
         with open(a.out, "w") as f:
