@@ -77,6 +77,29 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+def profiled_traffic(a, steps_per_launch):
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
+    scaled from its bytes per step; None when the kernel source has changed
+    since the capture (hash recorded in the summary) or the workload differs."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", "plate_kernel_fused_64plates_200x50.md")
+    if not os.path.exists(path) or (a.n_inst, a.n_phi, a.n_psi) != (64, 200, 50):
+        return None
+    text = open(path).read()
+    m_src = re.search(r"kernel-source: (\S+) sha256 ([0-9a-f]+)", text)
+    m_tr = re.search(r"traffic_bytes_per_step: (\d+)", text)
+    if not (m_src and m_tr):
+        return None
+    src = os.path.join(ROOT, m_src.group(1))
+    if not os.path.exists(src):
+        return None
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if not digest.startswith(m_src.group(2)):
+        return None
+    return float(m_tr.group(1)) * steps_per_launch
+
+
 # ----------------------------------------------------------------- inputs
 
 def _prepare_one(args):
@@ -386,8 +409,11 @@ def main():
     achieved = (d_bytes / n_l) / ((d_ms / n_l) * 1e-3) / 1e9 if n_l else 0.0
     names = {0: "plate_kernel<1> forward", 1: "plate_kernel<1> recompute",
              2: "plate_kernel<2> reverse", 4: "plate_kernel<3> fused reverse + recompute"}
+    traffic = profiled_traffic(a, a.K) if dom == 4 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
+                "traffic_source": ("profiles/plate_kernel_fused_64plates_200x50.md "
+                                   "(ncu, bytes per step x steps per launch)") if traffic else None,
                 "kernel": names[dom], "peak_source": f"{peak_kind} hbm_gbs",
                 "kernel_share_of_step": tot_ms / ms_total if ms_total else None,
                 "per_launch_ms": d_ms / max(n_l, 1),

@@ -571,13 +571,16 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                         for (int o = tpk >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                         if (kact && c4 == 0) red[kl * 4 + dd] = v;
                     }
+                    // slot 3: kappa of the stress mode, so the force loop reads shared memory only
+                    if (kact && c4 == 0) red[kl * 4 + 3] = P.kappa[d.k_off + ch.kl0 + kl];
                     consumer_bar();
                     // forces, per mode in class order (each thread owns distinct modes)
                     for (int mp = tid; mp < d.N; mp += kPlateThreads) {
                         const int su = P.perm[d.perm_off + mp];
                         float fa = 0.f, fb = 0.f, fr = 0.f;
+#pragma unroll 4
                         for (int q = 0; q < mc; ++q) {
-                            const float kap = P.kappa[d.k_off + ch.kl0 + q];
+                            const float kap = red[q * 4 + 3];
                             const float eta = red[q * 4 + 0];
                             const float u = S.U[((size_t)q * US + 0) * P.npad_max + mp];
                             if (!reverse) {
