@@ -100,6 +100,30 @@ def profiled_traffic(a, steps_per_launch):
     return float(m_tr.group(1)) * steps_per_launch
 
 
+# ----------------------------------------------------------------- ranks
+
+def shard_seed(rank):
+    """Instances are sharded by rank: every rank runs its own seeded batch
+    (independent problems, no collective on the data path)."""
+    return rank
+
+
+def max_over_ranks(ms, device, world):
+    """The job's time is the slowest rank's (all_reduce MAX; the only
+    collective of the benchmark)."""
+    import torch
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, n_inst, n_phi, sim_steps, ms_step):
+    """Plate mode-steps of all ranks per second of the slowest rank."""
+    return world * n_inst * n_phi * sim_steps / (ms_step * 1e-3)
+
+
 # ----------------------------------------------------------------- inputs
 
 def _prepare_one(args):
@@ -114,8 +138,8 @@ def prepare_inputs(a, rank):
     import concurrent.futures as cf
     import multiprocessing as mp
     from paper_2505_05940_gb300 import workloads as W
-    tgt, inits = W.adjoint_plates(seed=rank, n_inst=a.n_inst, n_phi=a.n_phi, n_psi=a.n_psi,
-                                  steps=a.sim_steps)
+    tgt, inits = W.adjoint_plates(seed=shard_seed(rank), n_inst=a.n_inst, n_phi=a.n_phi,
+                                  n_psi=a.n_psi, steps=a.sim_steps)
     jobs = [(tgt.instances[0], tgt.fs, tgt.steps, False)]
     jobs += [(i, inits.fs, inits.steps, True) for i in inits.instances]
     workers = a.workers or max(1, min(len(jobs), (os.cpu_count() or 2)))
@@ -388,14 +412,10 @@ def main():
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    ms_total = ev0.elapsed_time(ev1)
-    t_local = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    ms_total = float(t_local.item())
+    ms_total = max_over_ranks(ev0.elapsed_time(ev1), dev, world)
     ms_step = ms_total / a.steps
     units = world * a.n_inst * a.n_phi * a.sim_steps
-    value = units / (ms_step * 1e-3)
+    value = whole_job_value(world, a.n_inst, a.n_phi, a.sim_steps, ms_step)
     # roofline of the dominant kernel (plate kernel: forward, recompute, reverse,
     # fused reverse + recompute launches)
     stats = {w: sim.plan.kernel_stats(w) for w in (0, 1, 2, 4)}
