@@ -144,10 +144,14 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *inst, int n_inst,
 /*
  * Replace the per-mode coefficients of a plan without rebuilding it (the
  * coupling tensors and the work assignment stay): host FP64 arrays over all
- * modes in plan order (omega2, gamma, b, c; NULL keeps the current values),
- * tau [n_inst] (tension instances; NULL keeps) and kappa over all stress
- * modes in plan order (NULL keeps).  Validated like mdx_plan_create; on error
- * the plan is unchanged.  Synchronises the plan's device.
+ * modes in plan order (omega2 and gamma of Eq. 13-14, b, c; NULL keeps the
+ * current values), tau [n_inst] (tension instances; NULL keeps) and kappa of
+ * Eq. 9 over all stress modes in plan order (NULL keeps).  The FP32
+ * difference-form coefficients of Eq. 20-23 are recomputed from them.  Used
+ * by every iteration of an inverse fit (Sec. 4.3).  Validated like
+ * mdx_plan_create; on error the plan is unchanged.  Synchronises the plan's
+ * device.  Errors: MDX_ERR_ARG, MDX_ERR_UNSTABLE, MDX_ERR_NONFINITE,
+ * MDX_ERR_CUDA.
  */
 int mdx_plan_set_coefficients(mdx_plan *plan, const double *omega2, const double *gamma,
                               const double *b, const double *c, const double *tau,
@@ -225,6 +229,8 @@ int mdx_grad(mdx_plan *plan, const float *exc, const double *q0, const double *q
  * and reverse launches, and the number of persistent CTAs.
  */
 int mdx_plan_configure(mdx_plan *plan, int stage_bytes, int ring_stages);
+int mdx_plan_tiles(const mdx_plan *plan, int *stage_bytes, int *ring_fwd, int *ring_rev,
+                   int *ctas);
 
 /*
  * L2 residency of the coupling stream.  Every step re-reads the whole
@@ -234,12 +240,11 @@ int mdx_plan_configure(mdx_plan *plan, int stage_bytes, int ring_stages);
  * the L2 (129 MB on GB300) that fraction stays resident across steps.
  * fraction in [0, 1] (0 = no hint), or negative for the default: all of the
  * stream when it fits in 70 % of the L2, else the share that does.  Results
- * do not depend on it.  mdx_plan_l2_keep returns the fraction in use.
+ * do not depend on it (a cache hint; the paper has no counterpart).
+ * mdx_plan_l2_keep returns the fraction in use (0 for a NULL plan).
  */
 int mdx_plan_set_l2_keep(mdx_plan *plan, double fraction);
 double mdx_plan_l2_keep(const mdx_plan *plan);
-int mdx_plan_tiles(const mdx_plan *plan, int *stage_bytes, int *ring_fwd, int *ring_rev,
-                   int *ctas);
 
 /*
  * Kernel timing (tracing).  When enabled, every plate-kernel launch of the
