@@ -151,9 +151,11 @@ def _ptr(t):
 
 
 def _stream(stream=None):
-    import torch
-    s = stream if stream is not None else torch.cuda.current_stream()
-    return ctypes.c_void_p(s.cuda_stream)
+    """cudaStream_t of a torch stream (default: torch's current stream)."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
 
 
 class Plan:

@@ -564,3 +564,20 @@ def test_mlp_oracle_exact_on_small_integers():
     y, _ = MO.forward(Ws, bs, x, bf16=True)
     h = np.maximum(x @ Ws[0].T + bs[0], 0)
     np.testing.assert_array_equal(y, h @ Ws[1].T + bs[1])
+
+
+@pytest.mark.parametrize("n,m,f0", [(48, 12, 200.0), (100, 30, 50.0)])
+def test_parity_cases_are_well_conditioned(n, m, f0):
+    """A 1e-12 relative change of the excitation moves the FP64 output by far
+    less than the 1e-5 parity tolerance, so agreement to 1e-5 measures the
+    arithmetic and not the sensitivity of the system."""
+    from paper_2505_05940_gb300 import workloads as W
+    steps = 4410
+    wl = W.plate_100x30() if n == 100 else W.tiny_random(n + 3, "plate", n, m, steps=steps)
+    inst = wl.instances[0]
+    inst.F0 = f0
+    oi = PO.build_instance(inst, wl.fs, steps, coupling=CO.oracle_coupling)
+    a = oracle.forward(oi, steps=steps)["y"]
+    b = oracle.forward(oi, steps=steps, e=oi.e[:steps] * (1.0 + 1e-12))["y"]
+    d = np.linalg.norm(a - b) / np.linalg.norm(a)
+    assert d < 1e-9, d
