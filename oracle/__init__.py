@@ -11,7 +11,8 @@ Contents:
   modal_oracle.c     Stormer-Verlet time stepping (Eq. 20) with the tension
                      (Eq. 8) and von Karman (Eq. 9) forces, pickup, and a
                      hand-written reverse (adjoint) recursion, all FP64.
-  physics_oracle.py  modes, Eq. 13-14 and Eq. 21-23 coefficients, projections.
+  physics_oracle.py  modes, Eq. 13-14, Eq. 21-23 (Stormer-Verlet) and Eq. 15-19
+                     (impulse invariance) coefficients, projections.
   coupling_oracle.py H and C tensors (Eq. 10-11) by 2D quadrature.
   mlp_oracle.py      FP64 forward/backward of the proposal MLP.
   stft_oracle.py     multi-resolution log-STFT loss (Eq. 24).
@@ -163,6 +164,27 @@ def coefficient_grads(oi, adj, T):
     dp_dgm = (-1.0 / T ** 2 + gm / T) * dr_dg + oi.r / T
     d_omega2 = adj["dg"] * dg_dw2
     d_gamma = adj["dg"] * dg_dgm + adj["dp"] * dp_dgm + adj["dr"] * dr_dg
+    return d_omega2, d_gamma
+
+
+def coefficient_grads_tf(oi, adj, T):
+    """Chain rule from (g, p, r) to (omega^2, gamma) for the impulse-invariant
+    coefficients (oscillatory modes, omega > gamma):
+      g = 2 e^{-gamma T} cos(w~ T), p = -e^{-2 gamma T},
+      r = T e^{-gamma T} sin(w~ T) / w~,  w~^2 = omega^2 - gamma^2."""
+    w2, gm = oi.omega2, oi.gamma
+    wt = np.sqrt(w2 - gm ** 2)
+    e1 = np.exp(-gm * T)
+    g, r = oi.g, oi.r
+    # d/dw~ of sin(w~ T)/w~
+    ds = (T * np.cos(wt * T) * wt - np.sin(wt * T)) / wt ** 2
+    dg_dw2 = -T * e1 * np.sin(wt * T) / wt          # = -r
+    dg_dgm = -T * g + 2.0 * e1 * np.sin(wt * T) * T * gm / wt
+    dp_dgm = -2.0 * T * oi.p
+    dr_dw2 = T * e1 * ds / (2.0 * wt)
+    dr_dgm = -T * r - T * e1 * ds * gm / wt
+    d_omega2 = adj["dg"] * dg_dw2 + adj["dr"] * dr_dw2
+    d_gamma = adj["dg"] * dg_dgm + adj["dp"] * dp_dgm + adj["dr"] * dr_dgm
     return d_omega2, d_gamma
 
 

@@ -11,6 +11,8 @@ Everything here follows the paper's statement of the problem:
     and the damping family of Eq. 14 written gamma = sigma0 + sigma1 omega^2;
   * Stormer-Verlet coefficients r, g, p, Sec. 3.2, Eqs. 21-23, evaluated exactly
     as printed;
+  * impulse-invariant (transfer-function) coefficients, Sec. 3.2, Eq. 15-19,
+    as the same three-term recursion (see tf_coefficients for the readings);
   * tension-modulation coefficients, Sec. 3.1, Eq. 4 (tau_string = EA / 2L,
     tau_membrane = E h / (2 Lx Ly (1 - nu^2))), divided by rho for the modal form;
   * von Karman scale E / (2 rho zeta^4) of Sec. 3.1, Eq. 9 (volumetric rho);
@@ -102,6 +104,39 @@ def tau_prime(inst):
     return 0.0
 
 
+def tf_coefficients(omega2, gamma, T):
+    """Impulse-invariant discretisation of each modal oscillator (Sec. 3.2,
+    Eq. 15-19), returned as (g, p, r) of the same three-term recursion
+    q^{n+1} = g q^n + p q^{n-1} + r F^n that Eq. 20 uses.
+
+    The roots of z^2 + a1 z + a2 are exp((-gamma +- i w~) T), so
+    g = -a1 = 2 exp(-gamma T) cos(w~ T) and p = -a2 = -exp(-2 gamma T).  Two
+    readings of the printed Eq. 19: the recursion takes -a1, -a2 (the
+    denominator's roots, not the printed signs), and b1 carries the factor T
+    that impulse invariance gives a sampled force (the printed 1/rho is part
+    of the modal force here): r = T exp(-gamma T) sin(w~ T) / w~, with
+    w~ = sqrt(omega^2 - gamma^2).  Over-damped modes (gamma > omega) use the
+    hyperbolic forms, the critically damped limit sin(w~ T)/w~ -> T."""
+    w2 = np.asarray(omega2, np.float64)
+    gm = np.asarray(gamma, np.float64)
+    d = w2 - gm ** 2
+    e1 = np.exp(-gm * T)
+    g = np.empty_like(d)
+    s = np.empty_like(d)          # sin(w~ T) / w~ (or its hyperbolic / limit form)
+    osc, over = d > 0, d < 0
+    wt = np.sqrt(np.abs(d))
+    g[osc] = 2.0 * e1[osc] * np.cos(wt[osc] * T)
+    s[osc] = np.sin(wt[osc] * T) / wt[osc]
+    g[over] = 2.0 * e1[over] * np.cosh(wt[over] * T)
+    s[over] = np.sinh(wt[over] * T) / wt[over]
+    crit = ~(osc | over)
+    g[crit] = 2.0 * e1[crit]
+    s[crit] = T
+    p = -np.exp(-2.0 * gm * T)
+    r = T * e1 * s
+    return g, p, r
+
+
 def strike_signal(inst, fs, steps):
     """Raised-cosine force pulse F(t) = F0/2 (1 - cos(2 pi t / tw)), 0 <= t <= tw,
     sampled at t = n T."""
@@ -162,12 +197,15 @@ def n_psi_after_truncation(n_psi, n_phi, n_phi_eff):
     return min(n_psi, max(1, (n_psi * n_phi_eff) // n_phi))
 
 
-def build_instance(inst, fs, steps, coupling=None):
+def build_instance(inst, fs, steps, coupling=None, scheme="sv"):
     """All FP64 inputs of one instance.
 
     `coupling`, for plates, is a callable (inst, labels, n_psi) -> (H, zeta4)
     returning the coupling tensor of Sec. 3.1, Eq. 10 for the given transverse
-    mode labels, and the Airy eigenvalues zeta^4.
+    mode labels, and the Airy eigenvalues zeta^4.  `scheme` selects the
+    time discretisation: "sv" (Stormer-Verlet, Eq. 20-23) or "tf" (impulse
+    invariance, Eq. 15-19; the same mode truncation is applied so the two
+    schemes see the same modes).
     """
     T = 1.0 / fs
     if inst.kind == "string":
@@ -180,7 +218,10 @@ def build_instance(inst, fs, steps, coupling=None):
     n_eff = int(np.argmin(keep)) if not keep.all() else len(keep)
     labels, lam, omega2 = labels[:n_eff], lam[:n_eff], omega2[:n_eff]
     gamma = inst.sigma0 + inst.sigma1 * omega2
-    g, p, r = sv_coefficients(omega2, gamma, T)
+    if scheme == "tf":
+        g, p, r = tf_coefficients(omega2, gamma, T)
+    else:
+        g, p, r = sv_coefficients(omega2, gamma, T)
     if inst.kind == "string":
         c = mode_shape_string(inst, labels, inst.pickup[0])
         bshape = mode_shape_string(inst, labels, inst.strike[0])

@@ -581,3 +581,148 @@ def test_parity_cases_are_well_conditioned(n, m, f0):
     b = oracle.forward(oi, steps=steps, e=oi.e[:steps] * (1.0 + 1e-12))["y"]
     d = np.linalg.norm(a - b) / np.linalg.norm(a)
     assert d < 1e-9, d
+
+
+# ----------------------------------------------------------------- spectral losses
+
+def test_stft_oracle_tone_at_bin_centre():
+    """A unit cosine at an exact bin frequency gives |STFT| = n_fft / 4 at that
+    bin for every interior frame (sum of the periodic Hann window / 2)."""
+    from oracle import stft_oracle as SO
+    n_fft, k = 256, 17
+    t = np.arange(4096)
+    x = np.cos(2 * np.pi * k * t / n_fft + 0.3)
+    Y = SO.stft_mag(x, n_fft)
+    interior = Y[:, 4:-4]
+    np.testing.assert_allclose(interior[k], n_fft / 4, rtol=1e-12)
+    assert np.all(interior[k + 2:] < 1e-9 * n_fft)
+
+
+def test_spectral_losses_closed_forms():
+    from oracle import stft_oracle as SO
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(3000)
+    # spectral convergence of a scaled copy is |a - 1|
+    assert SO.spectral_convergence(0.7 * x, x) == pytest.approx(0.3, rel=1e-12)
+    # log-STFT distance of a scaled copy is |log a| where eps is negligible
+    big = 1e6 * x
+    assert SO.log_stft_l1(2.0 * big, big, 256) == pytest.approx(math.log(2.0), rel=1e-6)
+    # optimal transport between two pure tones: spectra concentrate on their
+    # bins, W1 approaches the bin distance
+    t = np.arange(8192)
+    a = np.cos(2 * np.pi * 40 * t / 1024)
+    b = np.cos(2 * np.pi * 52 * t / 1024)
+    assert SO.spectral_ot(a, b, 1024) == pytest.approx(12.0, rel=0.02)
+
+
+def test_library_losses_match_oracle():
+    """losses.py (torch, CPU, FP64) equals the numpy oracle."""
+    torch = pytest.importorskip("torch")
+    from oracle import stft_oracle as SO
+    from paper_2505_05940_gb300 import losses
+    rng = np.random.default_rng(9)
+    y = rng.standard_normal((2, 5000)) * 1e-3
+    t = rng.standard_normal((2, 5000)) * 1e-3
+    Y, T = torch.tensor(y), torch.tensor(t)
+    got = losses.multires_log_stft(Y, T).numpy()
+    ref = [SO.multires_log_stft(y[i], t[i]) for i in range(2)]
+    np.testing.assert_allclose(got, ref, rtol=1e-10)
+    np.testing.assert_allclose(losses.spectral_convergence(Y, T).numpy(),
+                               [SO.spectral_convergence(y[i], t[i]) for i in range(2)], rtol=1e-10)
+    np.testing.assert_allclose(losses.spectral_ot(Y, T).numpy(),
+                               [SO.spectral_ot(y[i], t[i]) for i in range(2)], rtol=1e-9)
+
+
+# ----------------------------------------------------------------- impulse-invariant scheme
+
+def _single_modes(omega2, gamma, T, steps, q0, qm1, e=None):
+    n = len(omega2)
+    g, p, r = PO.tf_coefficients(omega2, gamma, T)
+    return PO.OracleInstance(kind="string", N=n, M=0, labels=np.arange(1, n + 1).reshape(-1, 1),
+                             lam=np.ones(n), omega2=np.asarray(omega2, float),
+                             gamma=np.asarray(gamma, float), g=g, p=p, r=r, b=np.ones(n),
+                             c=np.ones(n), taup=0.0,
+                             e=np.zeros(steps) if e is None else e,
+                             q0=np.asarray(q0, float), qm1=np.asarray(qm1, float))
+
+
+def _free_continuous(w2, gm, t):
+    """q(t) with q(0) = 1, q'(0) = 0 for q'' + 2 gm q' + w2 q = 0."""
+    d = w2 - gm ** 2
+    if d > 0:
+        w = math.sqrt(d)
+        return np.exp(-gm * t) * (np.cos(w * t) + gm / w * np.sin(w * t))
+    if d < 0:
+        k = math.sqrt(-d)
+        return np.exp(-gm * t) * (np.cosh(k * t) + gm / k * np.sinh(k * t))
+    return np.exp(-gm * t) * (1.0 + gm * t)
+
+
+def test_tf_free_response_is_exact_at_the_samples():
+    """Impulse invariance puts the discrete poles at exp(s T): the free
+    response equals the continuous solution at every sample, for any omega T
+    (including omega T > 2, where Stormer-Verlet is unstable), and for
+    under-, critically and over-damped modes."""
+    T = 1.0 / 44100.0
+    w2 = np.array([(0.3 / T) ** 2, (1.7 / T) ** 2, (2.9 / T) ** 2, 400.0 ** 2, 900.0 ** 2, 300.0 ** 2])
+    gm = np.array([5.0, 40.0, 1e3, 400.0, 1.2e3, 100.0])
+    gm[3] = math.sqrt(w2[3])                     # critically damped
+    steps = 4000
+    q0 = np.ones(len(w2))
+    qm1 = np.array([_free_continuous(w2[i], gm[i], -T) for i in range(len(w2))])
+    oi = _single_modes(w2, gm, T, steps, q0, qm1)
+    traj = oracle.forward(oi, steps=steps, want_traj=True)["traj"]
+    t = np.arange(-1, steps + 1) * T
+    for i in range(len(w2)):
+        ref = _free_continuous(w2[i], gm[i], t)
+        np.testing.assert_allclose(traj[:, i], ref, rtol=0, atol=1e-11 * np.abs(ref).max())
+
+
+def test_tf_impulse_response_is_the_sampled_continuous_one():
+    """A unit force sample at n = 0 from rest gives q^n = T h(nT), with
+    h(t) = exp(-gamma t) sin(w~ t) / w~ the continuous impulse response."""
+    T = 1.0 / 48000.0
+    w2 = np.array([(2 * math.pi * 440.0) ** 2, (2 * math.pi * 9000.0) ** 2])
+    gm = np.array([3.0, 250.0])
+    steps = 3000
+    e = np.zeros(steps)
+    e[0] = 1.0
+    oi = _single_modes(w2, gm, T, steps, np.zeros(2), np.zeros(2), e=e)
+    traj = oracle.forward(oi, steps=steps, want_traj=True)["traj"]
+    n = np.arange(-1, steps + 1)
+    for i in range(2):
+        wt = math.sqrt(w2[i] - gm[i] ** 2)
+        h = np.where(n > 0, np.exp(-gm[i] * n * T) * np.sin(wt * n * T) / wt, 0.0)
+        # FP64 rounding of the recursion stays below 1e-9 of the peak T / w~
+        np.testing.assert_allclose(traj[:, i], T * h, rtol=0, atol=1e-9 * T / wt)
+
+
+def test_tf_coefficient_grads_match_central_fd():
+    """d L / d omega^2 and d L / d gamma through the impulse-invariant
+    coefficients (oracle adjoint + chain rule) against central differences
+    of the FP64 forward, on a nonlinear string."""
+    wl = W.tiny_random(5, "string", 8, steps=600, fs=48000.0)
+    T = 1.0 / wl.fs
+    oi = PO.build_instance(wl.instances[0], wl.fs, wl.steps, scheme="tf")
+    rng = np.random.default_rng(2)
+    ybar = rng.standard_normal(wl.steps)
+
+    def loss(w2, gm):
+        o = PO.OracleInstance(**{**oi.__dict__})
+        o.omega2, o.gamma = w2, gm
+        o.g, o.p, o.r = PO.tf_coefficients(w2, gm, T)
+        return float(ybar @ oracle.forward(o, steps=wl.steps)["y"])
+
+    adj = oracle.adjoint(oi, ybar)
+    dw2, dgm = oracle.coefficient_grads_tf(oi, adj, T)
+    for mu in (0, 3, 7):
+        h = 1e-6 * oi.omega2[mu]
+        e = np.zeros(oi.N)
+        e[mu] = h
+        fd = (loss(oi.omega2 + e, oi.gamma) - loss(oi.omega2 - e, oi.gamma)) / (2 * h)
+        assert dw2[mu] == pytest.approx(fd, rel=1e-5, abs=1e-12 * abs(fd) + 1e-30)
+        hg = 1e-5 * max(oi.gamma[mu], 1e-3)
+        e = np.zeros(oi.N)
+        e[mu] = hg
+        fdg = (loss(oi.omega2, oi.gamma + e) - loss(oi.omega2, oi.gamma - e)) / (2 * hg)
+        assert dgm[mu] == pytest.approx(fdg, rel=1e-5, abs=1e-9 * abs(fdg) + 1e-30)
