@@ -54,6 +54,12 @@ extern "C" {
 #define MDX_KIND_TENSION 0     /* string (Kirchhoff-Carrier) or membrane (Berger) */
 #define MDX_KIND_PLATE 1       /* von Karman plate */
 
+/* Time discretisation of the modal oscillators (Sec. 3.2). */
+#define MDX_SCHEME_SV 0        /* Stormer-Verlet, Eq. 20-23 (default) */
+#define MDX_SCHEME_TF 1        /* impulse invariance, Eq. 15-19: the recursion takes the
+                                  denominator's roots (-a1, -a2) and b1 carries the factor T
+                                  of a sampled force; oscillatory modes only (omega > gamma) */
+
 #define MDX_MAX_PHI 1024       /* transverse modes per instance */
 #define MDX_MAX_PSI 1024       /* stress modes per instance */
 
@@ -117,6 +123,7 @@ typedef struct mdx_options {
                           call reports MDX_ERR_TIMEOUT (fault-path tests);
                           bit 1: run the gradient as separate recompute and reverse launches
                           instead of the fused sweep (equivalence tests); 0 in normal use */
+    int scheme;        /* MDX_SCHEME_SV (default) or MDX_SCHEME_TF */
 } mdx_options;
 
 typedef struct mdx_plan mdx_plan;
@@ -156,6 +163,29 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *inst, int n_inst,
 int mdx_plan_set_coefficients(mdx_plan *plan, const double *omega2, const double *gamma,
                               const double *b, const double *c, const double *tau,
                               const double *kappa);
+
+/*
+ * Host FP64 coefficients of the difference form the kernels step (Sec. 3.2):
+ *   v^{n+1} = v^n - eps v^n - rho q^n + r F^n,  q^{n+1} = q^n + v^{n+1},
+ * i.e. the recursion q^{n+1} = g q^n + p q^{n-1} + r F^n of Eq. 20 (scheme
+ * MDX_SCHEME_SV, Eq. 21-23) or of Eq. 19 (MDX_SCHEME_TF, Eq. 16-18) with
+ * eps = 1 + p and rho = 1 - g - p, for n modes of period T.  Arrays are host
+ * memory of n doubles.  Errors: MDX_ERR_ARG (null array, unknown scheme, T <= 0),
+ * MDX_ERR_UNSTABLE (SV: omega T >= 2; TF: omega <= gamma; either: gamma < 0).
+ */
+int mdx_difference_coefficients(int scheme, int n, const double *omega2, const double *gamma,
+                                double T, double *eps, double *rho, double *r);
+
+/*
+ * Host FP64 chain rule from the adjoint sums of the reverse sweep,
+ * A = sum a^{n+1} q^n, V = sum a^{n+1} v^n, F = sum a^{n+1} F^n (so that
+ * dL/d rho = -A, dL/d eps = -V, dL/d r = F), to dL/d omega^2 and dL/d gamma
+ * for the scheme's coefficients; the gradient epilogue of mdx_grad runs the
+ * same function on the device.  Arrays of n doubles, host memory.
+ */
+int mdx_coefficient_grads(int scheme, int n, const double *omega2, const double *gamma,
+                          double T, const double *A, const double *V, const double *F,
+                          double *d_omega2, double *d_gamma);
 
 /* Release every resource of the plan (synchronises its device first). */
 int mdx_plan_destroy(mdx_plan *plan);

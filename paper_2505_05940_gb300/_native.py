@@ -28,7 +28,8 @@ EXPORTED = ("mdx_last_error", "mdx_version", "mdx_plan_create", "mdx_plan_destro
             "mdx_plan_kernel_stats", "mdx_plan_reset_stats", "mdx_plan_configure",
             "mdx_plan_tiles", "mdx_simulate_strings_noalloc", "mdx_plan_set_coefficients",
             "mdx_mlp_act_elems", "mdx_mlp_work_elems", "mdx_mlp_forward", "mdx_mlp_backward",
-            "mdx_adam_step", "mdx_f32_to_bf16", "mdx_plan_set_l2_keep", "mdx_plan_l2_keep")
+            "mdx_adam_step", "mdx_f32_to_bf16", "mdx_plan_set_l2_keep", "mdx_plan_l2_keep",
+            "mdx_difference_coefficients", "mdx_coefficient_grads")
 
 
 class MdxError(RuntimeError):
@@ -53,7 +54,7 @@ class Options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("max_ctas", ctypes.c_int),
                 ("ring_stages", ctypes.c_int), ("stage_bytes", ctypes.c_int),
                 ("force_split", ctypes.c_int), ("wait_limit", ctypes.c_int),
-                ("debug_flags", ctypes.c_int)]
+                ("debug_flags", ctypes.c_int), ("scheme", ctypes.c_int)]
 
 
 MLP_MAX_LAYERS = 8
@@ -108,6 +109,8 @@ def load(build_if_missing: bool = True):
         L.mdx_coeffs_vjp.argtypes = [i32, _D, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, _D, _D, _D, _D, _D, _D, _D]
         L.mdx_plan_set_coefficients.argtypes = [vp, _D, _D, _D, _D, _D, _D]
+        L.mdx_difference_coefficients.argtypes = [i32, i32, _D, _D, ctypes.c_double, _D, _D, _D]
+        L.mdx_coefficient_grads.argtypes = [i32, i32, _D, _D, ctypes.c_double, _D, _D, _D, _D, _D]
         L.mdx_mlp_act_elems.argtypes = [ctypes.POINTER(MLPDesc), i32]
         L.mdx_mlp_act_elems.restype = sz
         L.mdx_mlp_work_elems.argtypes = [ctypes.POINTER(MLPDesc), i32]
@@ -167,7 +170,7 @@ class Plan:
     """
 
     def __init__(self, instances, device=0, max_ctas=0, ring_stages=0, stage_bytes=0,
-                 force_split=0, wait_limit=0, debug_flags=0, use_classes=True):
+                 force_split=0, wait_limit=0, debug_flags=0, use_classes=True, scheme="sv"):
         L = load()
         self._keep = []
         arr = (Instance * len(instances))()
@@ -214,7 +217,7 @@ class Plan:
                 else:
                     s.n_psi = 0
         opts = Options(device, max_ctas, ring_stages, stage_bytes, force_split, wait_limit,
-                       debug_flags)
+                       debug_flags, SCHEMES[scheme] if isinstance(scheme, str) else int(scheme))
         h = ctypes.c_void_p()
         check(L.mdx_plan_create(ctypes.byref(h), arr, len(instances), ctypes.byref(opts)))
         self._h = h
@@ -314,6 +317,32 @@ class Plan:
         check(load().mdx_grad(self._h, _ptr(exc), _ptr(q0), _ptr(qm1), int(steps),
                               _ptr(d_audio), int(K), _ptr(ckpt), _ptr(work), wb,
                               ctypes.byref(g), _ptr(status), _stream(stream)))
+
+
+SCHEMES = {"sv": 0, "tf": 1}
+
+
+def difference_coefficients(scheme, omega2, gamma, T):
+    """(eps, rho, r) of the difference form for the given scheme ('sv' | 'tf')."""
+    w2 = np.ascontiguousarray(omega2, dtype=np.float64)
+    gm = np.ascontiguousarray(gamma, dtype=np.float64)
+    eps, rho, r = (np.zeros_like(w2) for _ in range(3))
+    check(load().mdx_difference_coefficients(SCHEMES[scheme], len(w2), w2.ctypes.data_as(_D),
+                                             gm.ctypes.data_as(_D), float(T),
+                                             eps.ctypes.data_as(_D), rho.ctypes.data_as(_D),
+                                             r.ctypes.data_as(_D)))
+    return eps, rho, r
+
+
+def coefficient_grads(scheme, omega2, gamma, T, A, V, F):
+    """dL/d omega^2, dL/d gamma from the adjoint sums A, V, F (see include/mdx.h)."""
+    arr = [np.ascontiguousarray(x, dtype=np.float64) for x in (omega2, gamma, A, V, F)]
+    dw2, dgm = np.zeros_like(arr[0]), np.zeros_like(arr[0])
+    check(load().mdx_coefficient_grads(SCHEMES[scheme], len(arr[0]),
+                                       *[a.ctypes.data_as(_D) for a in arr[:2]], float(T),
+                                       *[a.ctypes.data_as(_D) for a in arr[2:]],
+                                       dw2.ctypes.data_as(_D), dgm.ctypes.data_as(_D)))
+    return dw2, dgm
 
 
 def coeffs_from_physics(lam, D, T0, rho, s0, s1):

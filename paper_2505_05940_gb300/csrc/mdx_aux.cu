@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "mdx_common.cuh"
+#include "mdx_scheme.cuh"
 
 namespace mdx {
 
@@ -81,21 +82,23 @@ __global__ void grad_epilogue_kernel(const GradEpilogue g) {
     for (int s = threadIdx.x; s < d.N; s += blockDim.x) {
         const long long m = d.mode_off + s;
         const double T = g.dt[m], w2 = g.omega2[m], gm = g.gamma[m];
-        const double den = 1.0 + gm * T;
-        const double r = T * T / den;
+        const SchemeCoef k = scheme_coef(g.scheme, w2, gm, T);
         auto acc = [&](int idx) {
             return (double)g.gacc[(long long)(2 * idx) * TM + m] -
                    (double)g.gacc[(long long)(2 * idx + 1) * TM + m];
         };
         const double A = acc(GA_A), V = acc(GA_V), F = acc(GA_F), E = acc(GA_E), C = acc(GA_C);
-        if (g.d_omega2) g.d_omega2[m] = -r * A;
-        if (g.d_gamma) g.d_gamma[m] = (T / (den * den)) * (-2.0 * V + T * T * (w2 * A - F));
-        if (g.d_b) g.d_b[m] = r * E;
+        double dw2, dgm;
+        scheme_grads(g.scheme, w2, gm, T, A, V, F, &dw2, &dgm);
+        if (g.d_omega2) g.d_omega2[m] = dw2;
+        if (g.d_gamma) g.d_gamma[m] = dgm;
+        if (g.d_b) g.d_b[m] = k.r * E;
         if (g.d_c) g.d_c[m] = C;
         const double a0 = (double)g.adj[m] + (double)g.adj[TM + m];
         const double mu0 = (double)g.adj[2 * TM + m];
         if (g.d_q0) g.d_q0[m] = a0;
-        if (g.d_qm1) g.d_qm1[m] = -((1.0 - gm * T) / den) * (a0 - mu0);
+        // q^{-1} enters through v^0 = q^0 - q^{-1}, carried with factor 1 - eps
+        if (g.d_qm1) g.d_qm1[m] = -(1.0 - k.eps) * (a0 - mu0);
     }
     if (threadIdx.x == 0) {
         if (g.d_tau) g.d_tau[i] = (d.kind == 0 && g.tacc) ? kval(g.tacc + 2 * i) : 0.0;

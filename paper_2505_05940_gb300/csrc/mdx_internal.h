@@ -260,6 +260,7 @@ struct GradEpilogue {
     const float *adj, *gacc, *kacc, *tacc;
     const double *dir_acc;
     const int *kperm;                   // internal stress index -> user index (per plate)
+    int scheme;                         // MDX_SCHEME_SV / MDX_SCHEME_TF
     double *d_omega2, *d_gamma, *d_b, *d_c, *d_q0, *d_qm1, *d_tau, *d_kappa, *d_dir;
 };
 cudaError_t launch_grad_epilogue(const GradEpilogue &g, int max_n, cudaStream_t s);

@@ -14,6 +14,7 @@
 
 #include "../../include/mdx.h"
 #include "mdx_internal.h"
+#include "mdx_scheme.cuh"
 
 using namespace mdx;
 
@@ -91,6 +92,7 @@ struct mdx_plan {
     float *d_state = nullptr;        // [4][total_modes]
     long long wait_limit = 1 << 22;
     int debug_flags = 0;
+    int scheme = MDX_SCHEME_SV;      // time discretisation (mdx_options.scheme)
     // optional per-launch timing of the plate kernel
     bool profiling = false;
     struct Rec {
@@ -145,7 +147,24 @@ int upload(mdx_plan *p, T **out, const T *host, size_t n) {
 
 bool finite(double x) { return std::isfinite(x); }
 
-int validate(const mdx_instance &I, int i) {
+// Stability and domain of one mode under the plan's scheme.
+int check_mode(int scheme, double w2, double gm, double T, int i, int m) {
+    if (!(w2 > 0.0)) return fail(MDX_ERR_ARG, "instance %d mode %d: omega2 must be > 0", i, m);
+    if (gm < 0.0)
+        return fail(MDX_ERR_UNSTABLE, "instance %d mode %d: gamma < 0 puts a pole in the right half-plane", i, m);
+    if (scheme == MDX_SCHEME_TF) {
+        if (!(w2 > gm * gm))
+            return fail(MDX_ERR_UNSTABLE,
+                        "instance %d mode %d: the impulse-invariant scheme needs omega > gamma", i, m);
+    } else if (std::sqrt(w2) * T >= 2.0) {
+        return fail(MDX_ERR_UNSTABLE,
+                    "instance %d mode %d: omega*dt = %.4f >= 2 (Stormer-Verlet stability bound)",
+                    i, m, std::sqrt(w2) * T);
+    }
+    return MDX_OK;
+}
+
+int validate(const mdx_instance &I, int i, int scheme) {
     if (I.kind != MDX_KIND_TENSION && I.kind != MDX_KIND_PLATE)
         return fail(MDX_ERR_ARG, "instance %d: unknown kind %d", i, I.kind);
     if (I.n_phi < 1 || I.n_phi > MDX_MAX_PHI)
@@ -157,14 +176,8 @@ int validate(const mdx_instance &I, int i) {
     for (int m = 0; m < I.n_phi; ++m) {
         if (!finite(I.omega2[m]) || !finite(I.gamma[m]) || !finite(I.b[m]) || !finite(I.c[m]))
             return fail(MDX_ERR_NONFINITE, "instance %d mode %d: non-finite coefficient", i, m);
-        if (!(I.omega2[m] > 0.0))
-            return fail(MDX_ERR_ARG, "instance %d mode %d: omega2 must be > 0", i, m);
-        if (I.gamma[m] < 0.0)
-            return fail(MDX_ERR_UNSTABLE, "instance %d mode %d: gamma < 0 puts a pole in the right half-plane", i, m);
-        if (std::sqrt(I.omega2[m]) * I.dt >= 2.0)
-            return fail(MDX_ERR_UNSTABLE,
-                        "instance %d mode %d: omega*dt = %.4f >= 2 (Stormer-Verlet stability bound)",
-                        i, m, std::sqrt(I.omega2[m]) * I.dt);
+        const int rc = check_mode(scheme, I.omega2[m], I.gamma[m], I.dt, i, m);
+        if (rc) return rc;
     }
     if (I.kind == MDX_KIND_TENSION) {
         if (!I.lambda) return fail(MDX_ERR_ARG, "instance %d: lambda is required for the tension kind", i);
@@ -251,14 +264,17 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
     if (n_inst < 1 || !I) return fail(MDX_ERR_ARG, "need at least one instance");
     mdx_options o{};
     if (opts) o = *opts;
+    if (o.scheme != MDX_SCHEME_SV && o.scheme != MDX_SCHEME_TF)
+        return fail(MDX_ERR_ARG, "unknown scheme %d", o.scheme);
     for (int i = 0; i < n_inst; ++i) {
-        int rc = validate(I[i], i);
+        int rc = validate(I[i], i, o.scheme);
         if (rc) return rc;
     }
     MDX_CUDA(cudaSetDevice(o.device), "cudaSetDevice");
     mdx_plan *p = new mdx_plan();
     p->device = o.device;
     p->n_inst = n_inst;
+    p->scheme = o.scheme;
     if (o.wait_limit > 0) p->wait_limit = o.wait_limit;
     p->debug_flags = o.debug_flags;
     auto bail = [&](int rc) {
@@ -287,13 +303,12 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
         p->dt[i] = S.dt;
         const double T = S.dt;
         for (int m = 0; m < S.n_phi; ++m) {
-            const double den = 1.0 + S.gamma[m] * T;
-            const double rr = T * T / den;
-            eps.push_back((float)(2.0 * S.gamma[m] * T / den));
-            const double rw = rr * S.omega2[m];
+            const SchemeCoef k = scheme_coef(p->scheme, S.omega2[m], S.gamma[m], T);
+            eps.push_back((float)k.eps);
+            const double rw = k.rho;
             rw2.push_back((float)rw);
             rw2lo.push_back((float)(rw - (double)(float)rw));
-            r.push_back((float)rr);
+            r.push_back((float)k.r);
             b.push_back((float)S.b[m]);
             c.push_back((float)S.c[m]);
             lam.push_back(S.kind == MDX_KIND_TENSION ? (float)S.lambda[m] : 0.f);
@@ -1230,6 +1245,7 @@ extern "C" int mdx_grad(mdx_plan *p, const float *exc, const double *q0, const d
     g.dir_acc = w.dir_acc;
     g.tacc = w.tacc;
     g.kperm = p->d_kperm;
+    g.scheme = p->scheme;
     if (out) {
         g.d_omega2 = out->d_omega2;
         g.d_gamma = out->d_gamma;
@@ -1253,6 +1269,38 @@ extern "C" int mdx_coeffs_from_physics(int n, const double *lambda, double D, do
         const double l = lambda[m];
         omega2[m] = (D * l * l + T0 * l) / rho;   // Sec. 3.2, Eq. 13
         gamma[m] = s0 + s1 * omega2[m];           // damping family of Eq. 14
+    }
+    return MDX_OK;
+}
+
+extern "C" int mdx_difference_coefficients(int scheme, int n, const double *omega2,
+                                           const double *gamma, double T, double *eps,
+                                           double *rho, double *r) {
+    if (scheme != MDX_SCHEME_SV && scheme != MDX_SCHEME_TF) return fail(MDX_ERR_ARG, "unknown scheme %d", scheme);
+    if (n < 0 || (n > 0 && (!omega2 || !gamma || !eps || !rho || !r))) return fail(MDX_ERR_ARG, "null argument");
+    if (!(T > 0.0) || !std::isfinite(T)) return fail(MDX_ERR_ARG, "T must be > 0");
+    for (int m = 0; m < n; ++m) {
+        const int rc = check_mode(scheme, omega2[m], gamma[m], T, 0, m);
+        if (rc) return rc;
+        const SchemeCoef k = scheme_coef(scheme, omega2[m], gamma[m], T);
+        eps[m] = k.eps;
+        rho[m] = k.rho;
+        r[m] = k.r;
+    }
+    return MDX_OK;
+}
+
+extern "C" int mdx_coefficient_grads(int scheme, int n, const double *omega2, const double *gamma,
+                                     double T, const double *A, const double *V, const double *F,
+                                     double *d_omega2, double *d_gamma) {
+    if (scheme != MDX_SCHEME_SV && scheme != MDX_SCHEME_TF) return fail(MDX_ERR_ARG, "unknown scheme %d", scheme);
+    if (n < 0 || (n > 0 && (!omega2 || !gamma || !A || !V || !F || !d_omega2 || !d_gamma)))
+        return fail(MDX_ERR_ARG, "null argument");
+    if (!(T > 0.0) || !std::isfinite(T)) return fail(MDX_ERR_ARG, "T must be > 0");
+    for (int m = 0; m < n; ++m) {
+        const int rc = check_mode(scheme, omega2[m], gamma[m], T, 0, m);
+        if (rc) return rc;
+        scheme_grads(scheme, omega2[m], gamma[m], T, A[m], V[m], F[m], d_omega2 + m, d_gamma + m);
     }
     return MDX_OK;
 }
@@ -1366,11 +1414,8 @@ extern "C" int mdx_plan_set_coefficients(mdx_plan *p, const double *omega2, cons
             const size_t g = d.mode_off + m;
             if (!std::isfinite(w2[g]) || !std::isfinite(gm[g]) || !std::isfinite(bb[g]) || !std::isfinite(cc[g]))
                 return fail(MDX_ERR_NONFINITE, "instance %d mode %d: non-finite coefficient", i, m);
-            if (!(w2[g] > 0.0)) return fail(MDX_ERR_ARG, "instance %d mode %d: omega2 must be > 0", i, m);
-            if (gm[g] < 0.0) return fail(MDX_ERR_UNSTABLE, "instance %d mode %d: gamma < 0", i, m);
-            if (std::sqrt(w2[g]) * T >= 2.0)
-                return fail(MDX_ERR_UNSTABLE, "instance %d mode %d: omega*dt = %.4f >= 2", i, m,
-                            std::sqrt(w2[g]) * T);
+            const int rc = check_mode(p->scheme, w2[g], gm[g], T, i, m);
+            if (rc) return rc;
         }
         if (!std::isfinite(tt[i]) || tt[i] < 0.0) return fail(MDX_ERR_ARG, "instance %d: tau must be finite and >= 0", i);
     }
@@ -1382,13 +1427,12 @@ extern "C" int mdx_plan_set_coefficients(mdx_plan *p, const double *omega2, cons
         const double T = p->dt[i];
         for (int m = 0; m < d.N; ++m) {
             const size_t g = d.mode_off + m;
-            const double den = 1.0 + gm[g] * T;
-            const double r = T * T / den;
-            const double rw = r * w2[g];
-            eps[g] = (float)(2.0 * gm[g] * T / den);
+            const SchemeCoef k = scheme_coef(p->scheme, w2[g], gm[g], T);
+            const double rw = k.rho;
+            eps[g] = (float)k.eps;
             rw2[g] = (float)rw;
             rwl[g] = (float)(rw - (double)(float)rw);
-            rr[g] = (float)r;
+            rr[g] = (float)k.r;
             bf[g] = (float)bb[g];
             cf[g] = (float)cc[g];
         }

@@ -150,3 +150,71 @@ def test_coupling_symmetry_classes():
     # full-basis eigensolver mixes the parity blocks at solver rounding, ~1e-10)
     Ho, _ = CO.coupling_H(inst, labels, 30)
     assert np.abs(Ho[~mask]).max() <= 1e-9 * np.abs(Ho).max()
+
+
+# ----------------------------------------------------------------- time schemes
+
+def _modes(seed, n=200):
+    rng = np.random.default_rng(seed)
+    T = 1.0 / 44100.0
+    w2 = (rng.uniform(0.001, 1.85, n) / T) ** 2
+    gm = rng.uniform(0.0, 1.0, n) * np.minimum(np.sqrt(w2) * 0.5, 2e3)
+    return w2, gm, T
+
+
+@pytest.mark.parametrize("scheme", ["sv", "tf"])
+def test_difference_coefficients_match_oracle(scheme):
+    """eps = 1 + p and rho = 1 - g - p of the oracle's three-term recursion
+    (Eq. 21-23 for Stormer-Verlet, Eq. 16-19 for impulse invariance)."""
+    w2, gm, T = _modes(1)
+    eps, rho, r = N.difference_coefficients(scheme, w2, gm, T)
+    f = PO.sv_coefficients if scheme == "sv" else PO.tf_coefficients
+    g, p, rr = f(w2, gm, T)
+    np.testing.assert_allclose(r, rr, rtol=1e-13)
+    np.testing.assert_allclose(eps, 1.0 + p, rtol=1e-9, atol=1e-15)
+    # 1 - g - p cancels in the oracle's form: compare at its rounding level
+    np.testing.assert_allclose(rho, 1.0 - g - p, rtol=1e-8, atol=4e-16)
+
+
+def test_sv_difference_coefficients_are_the_planned_ones():
+    """The Stormer-Verlet branch is the closed form the plan always used,
+    bit for bit (eps = 2 gamma T/(1+gamma T), r = T^2/(1+gamma T), rho = r omega^2)."""
+    w2, gm, T = _modes(2)
+    eps, rho, r = N.difference_coefficients("sv", w2, gm, T)
+    den = 1.0 + gm * T
+    rr = T * T / den
+    assert np.array_equal(eps, 2.0 * gm * T / den)
+    assert np.array_equal(r, rr)
+    assert np.array_equal(rho, rr * w2)
+
+
+@pytest.mark.parametrize("scheme", ["sv", "tf"])
+def test_coefficient_grads_match_oracle_chain_rule(scheme):
+    """The chain rule the gradient epilogue runs equals the oracle's (which
+    is pinned against finite differences), with the adjoint sums mapped
+    through eps = 1 + p, rho = 1 - g - p: A = dL/dg, V = dL/dg - dL/dp,
+    F = dL/dr."""
+    import oracle
+    w2, gm, T = _modes(3)
+    rng = np.random.default_rng(4)
+    dg, dp, dr = (rng.standard_normal(len(w2)) for _ in range(3))
+    f = PO.sv_coefficients if scheme == "sv" else PO.tf_coefficients
+    g, p, r = f(w2, gm, T)
+    oi = PO.OracleInstance(kind="string", N=len(w2), M=0, labels=None, lam=None, omega2=w2,
+                           gamma=gm, g=g, p=p, r=r, b=None, c=None, taup=0.0, e=None, q0=None,
+                           qm1=None)
+    adj = dict(dg=dg, dp=dp, dr=dr)
+    ref = (oracle.coefficient_grads if scheme == "sv" else oracle.coefficient_grads_tf)(oi, adj, T)
+    got = N.coefficient_grads(scheme, w2, gm, T, dg, dg - dp, dr)
+    for a, b in zip(got, ref):
+        np.testing.assert_allclose(a, b, rtol=1e-7, atol=1e-12 * np.abs(b).max())
+
+
+def test_scheme_domains():
+    T = 1.0 / 44100.0
+    with pytest.raises(N.MdxError):       # Stormer-Verlet: omega T >= 2
+        N.difference_coefficients("sv", [(2.5 / T) ** 2], [1.0], T)
+    eps, rho, r = N.difference_coefficients("tf", [(2.5 / T) ** 2], [1.0], T)
+    assert np.isfinite(rho).all()         # impulse invariance has no such bound
+    with pytest.raises(N.MdxError):       # ... but needs an oscillatory mode
+        N.difference_coefficients("tf", [100.0], [20.0], T)
