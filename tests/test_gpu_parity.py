@@ -102,6 +102,15 @@ def test_string_sizes(n):
     check_parity([oracle_instance(wl.instances[0], wl.fs, wl.steps)], wl.fs, wl.steps)
 
 
+def test_membrane_400_modes():
+    """The largest mode count of the batched workload on the tension kernel
+    (13 modes per lane)."""
+    wl = W.tiny_random(400, "membrane", 400, steps=3000)
+    oi = oracle_instance(wl.instances[0], wl.fs, wl.steps)
+    assert oi.N == 400
+    check_parity([oi], wl.fs, wl.steps)
+
+
 @pytest.mark.parametrize("layout", ["dense", "classes"])
 @pytest.mark.parametrize("n,m", [(4, 1), (31, 3), (33, 8), (64, 16), (257, 9)])
 def test_plate_sizes(n, m, layout):
