@@ -104,7 +104,7 @@ def test_string_sizes(n):
 
 def test_membrane_400_modes():
     """The largest mode count of the batched workload on the tension kernel
-    (13 modes per lane)."""
+    (up to 16 modes per lane, 13 used)."""
     wl = W.tiny_random(400, "membrane", 400, steps=3000)
     oi = oracle_instance(wl.instances[0], wl.fs, wl.steps)
     assert oi.N == 400
