@@ -22,8 +22,8 @@ Everything here follows the paper's statement of the problem:
 from __future__ import annotations
 
 import math
-from dataclasses import dataclass, field
-from typing import List, Optional
+from dataclasses import dataclass
+from typing import Optional
 
 import numpy as np
 

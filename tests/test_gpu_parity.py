@@ -5,7 +5,6 @@ compensated state): relative L2 error <= 1e-5 on output audio and final
 state; gradients <= 1e-4 relative (normwise per gradient vector) against the
 oracle adjoint.  Inputs are the oracle's own FP64 coefficients with the
 coupling tensor rounded to FP32, the precision the library takes it in."""
-import copy
 
 import numpy as np
 import pytest

@@ -17,7 +17,7 @@ from oracle import coupling_oracle as CO
 from oracle import physics_oracle as PO
 from paper_2505_05940_gb300 import modal, workloads as W
 
-from test_gpu_parity import GTOL, TOL, classes_of, rel, to_plan
+from test_gpu_parity import GTOL, TOL, rel, to_plan
 
 
 def _oracle_tf(inst, fs, steps):

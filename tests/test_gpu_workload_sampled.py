@@ -4,7 +4,6 @@ One plate, built by the oracle, is checked against the FP64 oracle over the
 whole run; the gradient is checked through properties that hold at any size
 (the fused sweep equals separate launches bit for bit, and the result does
 not depend on the checkpoint interval)."""
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
