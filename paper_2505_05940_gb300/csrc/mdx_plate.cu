@@ -12,13 +12,22 @@
 // Execution model (one CTA per SM, cooperative launch so that all CTAs are
 // resident):
 //   * every CTA owns a list of work items (plate, contiguous stress-mode
-//     range); the host balances the H bytes of the items over the CTAs;
-//   * one producer warp streams the H rows of the CTA's items through a ring
-//     of shared-memory stages with TMA bulk copies (cp.async.bulk + mbarrier
-//     transaction counts).  H does not depend on the state, so the producer
-//     runs ahead across step boundaries while the consumers wait for q;
-//   * 8 consumer warps: thread t accumulates u_s for s = t, t+256, ...
-//     (rows of H^k are contiguous in s, so the reads are conflict free);
+//     range); the host splits the (plate, stress mode) units over the CTAs by
+//     a min-max partition of their cost (bytes plus a fixed cost per class
+//     chunk and per item);
+//   * one producer warp streams the CTA's coupling data through a ring of
+//     shared-memory stages with TMA bulk copies (cp.async.bulk + mbarrier
+//     transaction counts, an L2 evict_last policy on a fraction of the
+//     stream).  H does not depend on the state, so the producer runs ahead
+//     across step boundaries while the consumers wait for q;
+//   * 8 consumer warps.  Class layout (PAR): H^k_ij is nonzero only when
+//     class(i) ^ class(j) == class(k), and only those blocks are stored; a
+//     chunk of stress modes of one class is four super-blocks [p][k][s], and
+//     thread (k, column quad) accumulates the R right-hand sides over the
+//     rows.  Dense layout: float4 column strips x row groups over [p][s];
+//   * R = 1: forward / recompute; R = 2: reverse sweep ([q^n, w]); R = 3: the
+//     fused sweep, the reverse of segment s and the recompute of segment s-1
+//     ([q^n, w, q']) in the same pass over H;
 //   * plates split over several CTAs exchange partial forces through global
 //     memory, with a per-plate monotonic arrival counter (release / acquire,
 //     bounded spin); every contributor then applies the identical update so
@@ -673,7 +682,7 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                             }
                         }
                         if (active) {
-                            // slot 0: H q, slot 1: H w (reverse), slot 2: dH q (direction)
+                            // slot 0: H q, slot 1: H w (reverse)
                             if (mat == 0 && R > 1) {
                                 float *u0 = S.U + ((size_t)(kk * P.u_slots + 0) * G + g) * Np + 4 * c4;
                                 float *u1 = S.U + ((size_t)(kk * P.u_slots + 1) * G + g) * Np + 4 * c4;
@@ -689,7 +698,7 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                     }
                 }
                 consumer_bar();
-                // combine the row groups: u (H q), z (H w), t (dH q) for own modes
+                // combine the row groups: u (H q), z (H w) for own modes
                 float uu[kChunkK][kMaxSpt], zz[kChunkK][kMaxSpt];
 #pragma unroll
                 for (int kk = 0; kk < kChunkK; ++kk) {
