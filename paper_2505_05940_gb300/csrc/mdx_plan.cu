@@ -449,10 +449,11 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
             return t;
         };
         // Contiguous split: walk all (plate, stress mode) units in plan order
-        // and cut the running H-byte count into G equal parts; each CTA then
-        // holds at most one contiguous k range per plate.  A forced split
-        // (tests) or an overfull shared-memory state falls back to
-        // longest-processing-time assignment of explicit pieces.
+        // and cut them into G ranges (dense layout: equal H bytes; class
+        // layout: the min-max partition below); each CTA then holds at most
+        // one contiguous k range per plate.  A forced split (tests) or an
+        // overfull shared-memory state falls back to longest-processing-time
+        // assignment of explicit pieces.
         const int state_cap = 24 * 1024;   // 96 KB of item state per CTA at most
         double total = 0.0;
         long long total_kk = 0;
