@@ -45,3 +45,14 @@ def test_batch_split_and_concatenate():
     halves = np.concatenate([first, second], 0)
     for i in range(len(ois)):
         assert rel(halves[i], whole[i]) <= 1e-6, (i, rel(halves[i], whole[i]))
+
+
+def test_batched_workload_seeded_subset():
+    """The batched workload's own draws (first 24 instances with N_phi <= 120:
+    plates and membranes of uneven sizes, aspects on the shared grid, varied
+    thickness) in one plan, 2 205 steps, each against the oracle."""
+    wl = W.batched_ragged(seed=0, n_inst=512, steps=2205)
+    sel = [i for i, inst in enumerate(wl.instances) if inst.n_phi <= 120][:24]
+    ois = [oracle_instance(wl.instances[i], wl.fs, wl.steps) for i in sel]
+    assert {o.kind for o in ois} == {"plate", "membrane"}
+    check_parity(ois, wl.fs, wl.steps)
