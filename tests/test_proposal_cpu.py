@@ -85,3 +85,27 @@ def test_random_init_keeps_kind_and_aspect():
     assert r.shape == (10, 6)
     for t, lp in zip(wl.instances, r):
         assert lp[2] == pytest.approx(proposal.log_params(t)[2])
+
+
+def test_features_match_numpy_definition():
+    """Log-mel features (power STFT with a periodic Hann window, hop 256,
+    centred frames; HTK-mel triangles; log(mel + 1e-6); mean over 8 equal
+    frame segments) recomputed with numpy from the definition."""
+    from oracle import stft_oracle as SO
+    rng = np.random.default_rng(5)
+    x = (rng.standard_normal(11025) * 1e-2).astype(np.float32)
+    got = proposal.features(torch.tensor(x[None]), fs=44100.0)[0].numpy()
+    n_fft, fs = 1024, 44100.0
+    # the STFT oracle's frames use hop n_fft / 4 = 256, as the features do
+    P = SO.stft_mag(x.astype(np.float64), n_fft) ** 2
+    mel = lambda f: 2595.0 * np.log10(1.0 + f / 700.0)
+    imel = lambda m: 700.0 * (10.0 ** (m / 2595.0) - 1.0)
+    pts = imel(np.linspace(mel(20.0), mel(fs / 2), 130))
+    freqs = np.linspace(0.0, fs / 2, n_fft // 2 + 1)
+    fb = np.array([np.clip(np.minimum((freqs - pts[i]) / (pts[i + 1] - pts[i]),
+                                      (pts[i + 2] - freqs) / (pts[i + 2] - pts[i + 1])), 0, None)
+                   for i in range(128)])
+    m = np.log(fb @ P + 1e-6)
+    edges = np.linspace(0, m.shape[1], 9).astype(int)
+    ref = np.stack([m[:, edges[i]:max(edges[i + 1], edges[i] + 1)].mean(1) for i in range(8)], 1)
+    np.testing.assert_allclose(got, ref.reshape(-1), rtol=2e-4, atol=2e-4)
