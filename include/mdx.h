@@ -180,22 +180,31 @@ int mdx_difference_coefficients(int scheme, int n, const double *omega2, const d
  * Host FP64 chain rule from the adjoint sums of the reverse sweep,
  * A = sum a^{n+1} q^n, V = sum a^{n+1} v^n, F = sum a^{n+1} F^n (so that
  * dL/d rho = -A, dL/d eps = -V, dL/d r = F), to dL/d omega^2 and dL/d gamma
- * for the scheme's coefficients; the gradient epilogue of mdx_grad runs the
+ * for the scheme's coefficients (Sec. 3.2: Eq. 21-23 for MDX_SCHEME_SV,
+ * Eq. 16-18 for MDX_SCHEME_TF); the gradient epilogue of mdx_grad runs the
  * same function on the device.  Arrays of n doubles, host memory.
+ * Errors: as mdx_difference_coefficients.
  */
 int mdx_coefficient_grads(int scheme, int n, const double *omega2, const double *gamma,
                           double T, const double *A, const double *V, const double *F,
                           double *d_omega2, double *d_gamma);
 
-/* Release every resource of the plan (synchronises its device first). */
+/* Release every resource of the plan (synchronises its device first).
+ * Bookkeeping of this library (the paper has no plan object).  NULL is a
+ * no-op returning MDX_OK. */
 int mdx_plan_destroy(mdx_plan *plan);
 
-/* Plan geometry: number of instances, total modes, per-instance mode offset. */
+/* Plan geometry: number of instances, total modes, per-instance mode offset
+ * (the concatenation order of every per-mode array; bookkeeping, no
+ * counterpart in the paper).  Output pointers may be NULL.  Errors:
+ * MDX_ERR_ARG for a NULL plan. */
 int mdx_plan_info(const mdx_plan *plan, int *n_inst, long *total_modes,
                   long *mode_offset /* [n_inst] or NULL */);
 
 /* Bytes of the checkpoint buffer mdx_simulate writes for `steps` steps with
- * checkpoint interval K (state before steps 0, K, 2K, ...). */
+ * checkpoint interval K (state before steps 0, K, 2K, ...; the checkpointed
+ * adjoint of this library, the paper differentiates through its whole loop).
+ * Returns 0 for a NULL plan or steps, K <= 0. */
 size_t mdx_checkpoint_bytes(const mdx_plan *plan, int steps, int K);
 
 /*
@@ -228,11 +237,16 @@ typedef struct mdx_grads {
     double *d_dir;      /* [n_inst] <dL/dH, dH> for plates planned with dH (else 0) */
 } mdx_grads;
 
-/* Bytes of the workspace mdx_grad needs for (steps, K). */
+/* Bytes of the caller-owned device workspace mdx_grad needs for (steps, K):
+ * two K-step segment buffers, the adjoint state and the gradient
+ * accumulators.  Returns 0 for a NULL plan or K <= 0. */
 size_t mdx_grad_workspace_bytes(const mdx_plan *plan, int steps, int K);
 
 /*
- * Reverse-mode derivative of a scalar loss L(y) through the whole time loop.
+ * Reverse-mode derivative of a scalar loss L(y) through the whole time loop of
+ * Eq. 20 with the forces of Eq. 8-9 (the gradients the paper obtains by
+ * automatic differentiation for its inverse problems, Sec. 4.3), written as a
+ * hand-derived adjoint recursion.
  * Given dL/dy it runs the adjoint recursion backwards, segment by segment:
  * each K-step segment is recomputed from the checkpoint mdx_simulate wrote
  * (same arguments, same K), then swept in reverse.  With the class layout the
@@ -251,7 +265,8 @@ int mdx_grad(mdx_plan *plan, const float *exc, const double *q0, const double *q
              size_t work_bytes, const mdx_grads *out, int *status, void *stream);
 
 /*
- * Tile configuration of the plate kernel (used by the autotuner): TMA stage
+ * Tile configuration of the plate kernel (used by the autotuner; a
+ * performance control with no counterpart in the paper): TMA stage
  * size in bytes (multiple of 16, 0 = default 64 KB) and ring depth (0 = as
  * many stages as shared memory allows).  Takes effect for later launches;
  * fails with MDX_ERR_UNSUPPORTED if the stages do not fit in shared memory.
@@ -277,7 +292,8 @@ int mdx_plan_set_l2_keep(mdx_plan *plan, double fraction);
 double mdx_plan_l2_keep(const mdx_plan *plan);
 
 /*
- * Kernel timing (tracing).  When enabled, every plate-kernel launch of the
+ * Kernel timing (tracing; no counterpart in the paper, whose timings are
+ * wall-clock, Sec. 4.2).  When enabled, every plate-kernel launch of the
  * plan is bracketed by CUDA events on its launch stream.  mdx_plan_kernel_stats
  * synchronises those events and returns, for one launch class
  * (0 = forward, 1 = checkpoint recompute, 2 = reverse sweep, 3 = per-segment
@@ -325,28 +341,34 @@ typedef struct mdx_mlp {
 } mdx_mlp;
 
 /* Elements (uint16) of the hidden-activation buffer, and of the backward
- * work buffer, for a batch. */
+ * work buffer, for a batch (learned proposal, see above).  0 for invalid
+ * arguments. */
 size_t mdx_mlp_act_elems(const mdx_mlp *net, int batch);
 size_t mdx_mlp_work_elems(const mdx_mlp *net, int batch);
 
 /* y [batch][dL] (FP32) = net(x), x BF16 [batch][d0]; acts receives the hidden
- * activations (needed by the backward pass). */
+ * activations (needed by the backward pass).  Learned proposal, see above.
+ * Errors: MDX_ERR_ARG (layer count, widths, missing weights or buffers),
+ * MDX_ERR_CUDA (launch). */
 int mdx_mlp_forward(const mdx_mlp *net, int batch, const uint16_t *x, uint16_t *acts, float *y,
                     void *stream);
 
-/* Gradients of sum(dy . y) for the same x and acts: dW[l] FP32 [d_{l+1}][d_l],
+/* Learned proposal (see above).
+ * Gradients of sum(dy . y) for the same x and acts: dW[l] FP32 [d_{l+1}][d_l],
  * db[l] FP32 [d_{l+1}] (overwritten).  dy is rounded to BF16 once; the
  * back-propagated signals are BF16 like the activations. */
 int mdx_mlp_backward(const mdx_mlp *net, int batch, const uint16_t *x, const uint16_t *acts,
                      const float *dy, float *const *dW, float *const *db, uint16_t *work,
                      void *stream);
 
-/* One Adam step on n FP32 master weights w (moments m, v; step number t >= 1),
+/* Learned proposal training (see above; Adam as in the paper's fits, Sec. 4.3).
+ * One Adam step on n FP32 master weights w (moments m, v; step number t >= 1),
  * refreshing the BF16 copy w_bf16 (may be NULL). */
 int mdx_adam_step(long long n, float *w, uint16_t *w_bf16, const float *g, float *m, float *v,
                   float lr, float beta1, float beta2, float eps, int t, void *stream);
 
-/* Round-to-nearest-even FP32 -> BF16 of n elements. */
+/* Round-to-nearest-even FP32 -> BF16 of n elements (learned proposal inputs
+ * and weights).  Errors: MDX_ERR_ARG, MDX_ERR_CUDA. */
 int mdx_f32_to_bf16(long long n, const float *x, uint16_t *y, void *stream);
 
 /*
