@@ -391,15 +391,17 @@ def test_nonlinear_reduces_to_linear():
         np.testing.assert_allclose(out["traj"][2:, mu], x, rtol=0, atol=1e-12 * np.abs(x).max())
 
 
-def test_scheme_second_order_vs_dop853():
-    """Fig. 1's claim: the Stormer-Verlet solution of the tension-modulated
-    string converges to the DOP853 solution of Eq. 12 at second order in T."""
+@pytest.mark.parametrize("scheme", ["sv", "tf"])
+def test_scheme_second_order_vs_dop853(scheme):
+    """Fig. 1's claim: the Stormer-Verlet and the impulse-invariant solutions
+    of the tension-modulated string converge to the DOP853 solution of Eq. 12
+    at second order in T."""
     base = W.string_40().instances[0]
     base.n_phi = 12
     dur = 0.004
     errs = []
     for fs in (96000.0, 192000.0):
-        oi = PO.build_instance(base, fs, int(dur * fs))
+        oi = PO.build_instance(base, fs, int(dur * fs), scheme=scheme)
         # ODE: qdd + 2 gamma qd + w2 q = -fnl(q), q(0) = q0, qd(0) = 0
         def rhs(t, z):
             q, v = z[:oi.N], z[oi.N:]
