@@ -53,11 +53,12 @@ static double nl_force(const orc_model *m, const double *q, double *f, double *u
     for (int k = 0; k < M; ++k) {
         const double *Hk = m->H + (size_t)k * N * N;
         double e = 0.0;
-        for (int s = 0; s < N; ++s) {
-            double acc = 0.0;
-            for (int pp = 0; pp < N; ++pp) acc += Hk[(size_t)pp * N + s] * q[pp];
-            u[(size_t)k * N + s] = acc;
-        }
+        /* u_s = sum_p H_ps q_p, each sum taken over p = 0, 1, ... in order;
+           H^k is walked row by row (memory order only, same arithmetic) */
+        double *uk = u + (size_t)k * N;
+        for (int s = 0; s < N; ++s) uk[s] = 0.0;
+        for (int pp = 0; pp < N; ++pp)
+            for (int s = 0; s < N; ++s) uk[s] += Hk[(size_t)pp * N + s] * q[pp];
         for (int a = 0; a < N; ++a)
             for (int bb = 0; bb < N; ++bb) e += Hk[(size_t)a * N + bb] * q[a] * q[bb];
         eta[k] = e;
@@ -136,15 +137,16 @@ static void jac_vec(const orc_model *m, const double *q, const double *w, double
     for (int k = 0; k < M; ++k) {
         const double *Hk = m->H + (size_t)k * N * N;
         double uq = 0.0, uw = 0.0;
-        for (int s = 0; s < N; ++s) {
-            double au = 0.0, az = 0.0;
-            for (int pp = 0; pp < N; ++pp) {
-                au += Hk[(size_t)pp * N + s] * q[pp];
-                az += Hk[(size_t)pp * N + s] * w[pp];
+        /* u = H^k q, z = H^k w, each sum over p in order (row-by-row walk) */
+        for (int s = 0; s < N; ++s) { u[s] = 0.0; z[s] = 0.0; }
+        for (int pp = 0; pp < N; ++pp)
+            for (int s = 0; s < N; ++s) {
+                u[s] += Hk[(size_t)pp * N + s] * q[pp];
+                z[s] += Hk[(size_t)pp * N + s] * w[pp];
             }
-            u[s] = au; z[s] = az;
-            uq += au * q[s];
-            uw += au * w[s];
+        for (int s = 0; s < N; ++s) {
+            uq += u[s] * q[s];
+            uw += u[s] * w[s];
         }
         eta[k] = uq;
         /* d/dq [kappa eta u] w = kappa (2 u (u.w) + eta H w) */
