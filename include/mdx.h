@@ -376,8 +376,9 @@ int mdx_f32_to_bf16(long long n, const float *x, uint16_t *y, void *stream);
  * The paper has no counterpart: this entry point exists for callers that must
  * not call cudaMalloc, such as a real-time audio callback (cudaMalloc can
  * block for milliseconds and synchronises the device) or a plug-in whose host
- * application owns every device buffer.  It computes the same forward pass as
- * mdx_plan_create + mdx_simulate for MDX_KIND_TENSION instances, without a plan.
+ * application owns every device buffer.  For MDX_KIND_TENSION instances it
+ * computes, bit for bit, the forward pass of mdx_plan_create (scheme
+ * MDX_SCHEME_SV, the only scheme it offers) + mdx_simulate, without a plan.
  *   inst     [n_inst] host descriptions, all MDX_KIND_TENSION (H, kappa, dH unused)
  *   exc      device [n_inst][steps] FP32 excitation (NULL = zero)
  *   q0, qm1  device [total_modes] FP64 initial state (NULL = zero)
@@ -386,14 +387,19 @@ int mdx_f32_to_bf16(long long n, const float *x, uint16_t *y, void *stream);
  *   status   device [n_inst] int, as in mdx_simulate (NULL = not written)
  * Scratch: one fixed 1 MiB block of device memory per GPU, owned by the
  * library (a file-scope __device__ array held until the process exits).  It
- * bounds the problem: total modes <= (1 MiB - 76 B x n_inst) / 44 B (about
- * 23 800 modes for one instance); larger requests fail with MDX_ERR_UNSUPPORTED.  No call
- * allocates or frees device memory.  The first call on a device looks up the
- * block's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  Every call reuses the same
- * block: calls that overlap on the GPU (e.g. on two streams) race and must
- * be serialised.  Errors: MDX_ERR_ARG, MDX_ERR_UNSTABLE, MDX_ERR_NONFINITE,
- * MDX_ERR_UNSUPPORTED, MDX_ERR_CUDA (message in mdx_last_error).
+ * bounds the problem: for n instances, total modes must not exceed
+ *   (1048576 - align16(120 n) - align16(4 n) - 176) / 44   (rounded down,
+ *   align16(x) = x rounded up to a multiple of 16; 23 824 modes for n = 1);
+ * larger requests fail with MDX_ERR_UNSUPPORTED.  No call allocates or frees
+ * device memory.  The first call on a device looks up the block's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  The coefficient table computed on the host
+ * reaches the block inside the parameters of small copy kernels enqueued on
+ * `stream`, so no host buffer is read after the call returns.  Every call
+ * reuses the same block: calls that overlap on the GPU (e.g. on two streams)
+ * race and must be serialised.  Errors: MDX_ERR_ARG, MDX_ERR_UNSTABLE,
+ * MDX_ERR_NONFINITE, MDX_ERR_UNSUPPORTED, MDX_ERR_CUDA (message in
+ * mdx_last_error).
  */
 int mdx_simulate_strings_noalloc(const mdx_instance *inst, int n_inst, const float *exc,
                                  const double *q0, const double *qm1, int steps, float *audio,

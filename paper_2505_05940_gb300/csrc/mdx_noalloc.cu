@@ -17,6 +17,11 @@
 // runs on the first call, the first call on a device should happen before any
 // stream capture.
 //
+// The per-call table (instance descriptions and FP32 coefficients, computed
+// on the host) reaches the block inside the parameters of small copy kernels,
+// at most 31 KB per launch: no host buffer is read after the call returns and
+// no pageable host-to-device copy is issued.
+//
 // All calls share the block and it keeps whatever the last call wrote.
 // Nothing in it has to start at zero: each call writes every word it later
 // reads (instance table, coefficients, state).  Calls whose work overlaps on
@@ -25,12 +30,14 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <vector>
 
 #include "../../include/mdx.h"
 #include "mdx_internal.h"
+#include "mdx_scheme.cuh"
 
 using namespace mdx;
 
@@ -48,12 +55,29 @@ int noalloc_fail(int code, const char *msg) { return set_last_error(code, msg); 
 
 size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
+// The size limit stated in include/mdx.h counts 120 bytes per instance
+// descriptor.
+static_assert(sizeof(InstDesc) == 120, "update the no-allocation size limit in mdx.h");
+
+// One piece of the host table, carried by value in the kernel's parameters
+// (kernel parameters may hold up to 32 764 bytes).
+constexpr int kUploadWords = 7936;
+struct UploadChunk {
+    unsigned *dst;
+    int n;
+    unsigned w[kUploadWords];
+};
+
+__global__ void noalloc_upload_kernel(const __grid_constant__ UploadChunk c) {
+    for (int i = threadIdx.x; i < c.n; i += blockDim.x) c.dst[i] = c.w[i];
+}
+
 }  // namespace
 
 // Largest total mode count the fixed block can hold for n_inst instances.
 static long noalloc_max_modes(int n_inst) {
     if (n_inst < 1) return 0;
-    const size_t head = align16(n_inst * sizeof(InstDesc)) + align16(n_inst * sizeof(int));
+    const size_t head = align16((size_t)n_inst * sizeof(InstDesc)) + align16((size_t)n_inst * sizeof(int));
     if (head >= kNoAllocBytes) return 0;
     // 7 coefficient arrays + 4 state arrays, each 16-byte aligned
     return (long)((kNoAllocBytes - head - 11 * 16) / (11 * sizeof(float)));
@@ -92,7 +116,8 @@ extern "C" int mdx_simulate_strings_noalloc(const mdx_instance *inst, int n_inst
     if (TM > noalloc_max_modes(n_inst))
         return noalloc_fail(MDX_ERR_UNSUPPORTED,
                             "total modes exceed the fixed 1 MiB scratch block of the "
-                            "no-allocation entry point (at most (1 MiB - 76 B per instance) / 44 B)");
+                            "no-allocation entry point (at most (1048576 - align16(120 n) - "
+                            "align16(4 n) - 176) / 44 for n instances)");
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
@@ -134,23 +159,35 @@ extern "C" int mdx_simulate_strings_noalloc(const mdx_instance *inst, int n_inst
         list[i] = i;
         const double T = I.dt;
         for (int m = 0; m < I.n_phi; ++m) {
-            const double den = 1.0 + I.gamma[m] * T;
-            const double r = T * T / den;
-            const double rw = r * I.omega2[m];
-            cf[0 * cs + mo + m] = (float)(2.0 * I.gamma[m] * T / den);
-            cf[1 * cs + mo + m] = (float)rw;
-            cf[2 * cs + mo + m] = (float)r;
+            // the same FP32 coefficients as a plan of scheme MDX_SCHEME_SV
+            const ModeF32 k = mode_f32(MDX_SCHEME_SV, I.omega2[m], I.gamma[m], T);
+            cf[0 * cs + mo + m] = k.eps;
+            cf[1 * cs + mo + m] = k.rho_hi;
+            cf[2 * cs + mo + m] = k.r;
             cf[3 * cs + mo + m] = (float)I.b[m];
             cf[4 * cs + mo + m] = (float)I.c[m];
             cf[5 * cs + mo + m] = (float)I.lambda[m];
-            cf[6 * cs + mo + m] = (float)(rw - (double)(float)rw);
+            cf[6 * cs + mo + m] = k.rho_lo;
         }
         mo += I.n_phi;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned char *b = static_cast<unsigned char *>(base);
-    if (cudaMemcpyAsync(b, img.data(), img.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return noalloc_fail(MDX_ERR_CUDA, "copy into the scratch block failed");
+    {
+        // the table, in kernel-parameter pieces (its size is a multiple of 16 bytes)
+        static thread_local UploadChunk chunk;
+        const unsigned *words = reinterpret_cast<const unsigned *>(img.data());
+        const size_t n_words = img.size() / sizeof(unsigned);
+        for (size_t w0 = 0; w0 < n_words; w0 += kUploadWords) {
+            const int n = (int)std::min<size_t>(kUploadWords, n_words - w0);
+            chunk.dst = reinterpret_cast<unsigned *>(b) + w0;
+            chunk.n = n;
+            std::memcpy(chunk.w, words + w0, (size_t)n * sizeof(unsigned));
+            noalloc_upload_kernel<<<1, 256, 0, s>>>(chunk);
+            if (cudaGetLastError() != cudaSuccess)
+                return noalloc_fail(MDX_ERR_CUDA, "copy into the scratch block failed");
+        }
+    }
     if (status && cudaMemsetAsync(status, 0, n_inst * sizeof(int), s) != cudaSuccess)
         return noalloc_fail(MDX_ERR_CUDA, "clearing status failed");
     const float *dcf = reinterpret_cast<const float *>(b + off_coef);

@@ -303,12 +303,11 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
         p->dt[i] = S.dt;
         const double T = S.dt;
         for (int m = 0; m < S.n_phi; ++m) {
-            const SchemeCoef k = scheme_coef(p->scheme, S.omega2[m], S.gamma[m], T);
-            eps.push_back((float)k.eps);
-            const double rw = k.rho;
-            rw2.push_back((float)rw);
-            rw2lo.push_back((float)(rw - (double)(float)rw));
-            r.push_back((float)k.r);
+            const ModeF32 k = mode_f32(p->scheme, S.omega2[m], S.gamma[m], T);
+            eps.push_back(k.eps);
+            rw2.push_back(k.rho_hi);
+            rw2lo.push_back(k.rho_lo);
+            r.push_back(k.r);
             b.push_back((float)S.b[m]);
             c.push_back((float)S.c[m]);
             lam.push_back(S.kind == MDX_KIND_TENSION ? (float)S.lambda[m] : 0.f);
@@ -1428,12 +1427,11 @@ extern "C" int mdx_plan_set_coefficients(mdx_plan *p, const double *omega2, cons
         const double T = p->dt[i];
         for (int m = 0; m < d.N; ++m) {
             const size_t g = d.mode_off + m;
-            const SchemeCoef k = scheme_coef(p->scheme, w2[g], gm[g], T);
-            const double rw = k.rho;
-            eps[g] = (float)k.eps;
-            rw2[g] = (float)rw;
-            rwl[g] = (float)(rw - (double)(float)rw);
-            rr[g] = (float)k.r;
+            const ModeF32 k = mode_f32(p->scheme, w2[g], gm[g], T);
+            eps[g] = k.eps;
+            rw2[g] = k.rho_hi;
+            rwl[g] = k.rho_lo;
+            rr[g] = k.r;
             bf[g] = (float)bb[g];
             cf[g] = (float)cc[g];
         }

@@ -84,6 +84,23 @@ __host__ __device__ inline SchemeDeriv scheme_deriv(int scheme, double w2, doubl
     return d;
 }
 
+// FP32 coefficients of one mode as the kernels read them: eps, rho as an
+// unevaluated pair rho_hi + rho_lo (rho is subtracted from the state every
+// step, so its rounding error would otherwise shift the mode's frequency), r.
+struct ModeF32 {
+    float eps, rho_hi, rho_lo, r;
+};
+
+inline ModeF32 mode_f32(int scheme, double w2, double gm, double T) {
+    const SchemeCoef k = scheme_coef(scheme, w2, gm, T);
+    ModeF32 o;
+    o.eps = (float)k.eps;
+    o.rho_hi = (float)k.rho;
+    o.rho_lo = (float)(k.rho - (double)o.rho_hi);
+    o.r = (float)k.r;
+    return o;
+}
+
 // dL/d omega^2 and dL/d gamma from the adjoint sums (see above).
 __host__ __device__ inline void scheme_grads(int scheme, double w2, double gm, double T, double A,
                                              double V, double F, double *d_w2, double *d_gm) {
