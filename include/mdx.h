@@ -89,6 +89,20 @@ extern "C" {
  *            only the nonzero class blocks (a quarter of H).  The plan checks
  *            the pattern: an entry outside it larger than 1e-6 max|H^k| fails
  *            with MDX_ERR_ARG; smaller ones are treated as zero.
+ *   geom_group  plates of one geometry (> 0; 0 = none).  Plates with the same
+ *            id share their modes: for a simply supported rectangle of fixed
+ *            area and aspect ratio, a plate with fewer modes has a prefix of
+ *            the largest member's transverse and stress modes (Sec. 3, Eq. 2),
+ *            so its H (Eq. 10) is the leading block of the largest member's.
+ *            The plan checks that (bit for bit), and that the member with the
+ *            most transverse modes also has the most stress modes; classes are
+ *            required.  Unless mdx_options.group_engine is MDX_GROUP_OFF, such
+ *            plates are stepped together: per step and stress mode, H^k times
+ *            the group's states is one GEMM on the tensor cores (split TF32,
+ *            FP32 accumulation; error about 2^-21 of |H||q|, like FP32).
+ *            Plans with grouped plates simulate only: checkpoints and mdx_grad
+ *            fail with MDX_ERR_UNSUPPORTED (plan with MDX_GROUP_OFF to
+ *            differentiate them).
  * Stability: every mode needs omega_mu * dt < 2 (Eq. 20 is explicit);
  * otherwise mdx_plan_create fails with MDX_ERR_UNSTABLE naming the mode.
  */
@@ -108,6 +122,7 @@ typedef struct mdx_instance {
     const float *dH;
     const int *phi_class;
     const int *psi_class;
+    int geom_group;
 } mdx_instance;
 
 /* Plan options; zero-initialise for defaults. */
@@ -124,7 +139,13 @@ typedef struct mdx_options {
                           bit 1: run the gradient as separate recompute and reverse launches
                           instead of the fused sweep (equivalence tests); 0 in normal use */
     int scheme;        /* MDX_SCHEME_SV (default) or MDX_SCHEME_TF */
+    int group_engine;  /* plates with geom_group > 0: MDX_GROUP_TF32X3 (default) steps each
+                          group with one shared coupling tensor on the tensor cores;
+                          MDX_GROUP_OFF gives every plate its own copy (FP32 CUDA-core path) */
 } mdx_options;
+
+#define MDX_GROUP_TF32X3 0
+#define MDX_GROUP_OFF 1
 
 typedef struct mdx_plan mdx_plan;
 
@@ -298,7 +319,9 @@ double mdx_plan_l2_keep(const mdx_plan *plan);
  * synchronises those events and returns, for one launch class
  * (0 = forward, 1 = checkpoint recompute, 2 = reverse sweep, 3 = per-segment
  * contraction of the direction tensor, 4 = fused sweep: the adjoint of one
- * segment and the recompute of the previous one in the same launch), the
+ * segment and the recompute of the previous one in the same launch,
+ * 5 = grouped plates on the tensor cores: bytes are the nonzero class blocks
+ * of each group's shared coupling tensor, one pass per step), the
  * number of launches, their summed device time in ms and their summed
  * algorithmic bytes (coupling-tensor bytes each launch must stream: one pass
  * over H per step; the direction tensor is counted by class 3).
@@ -321,6 +344,95 @@ int mdx_coeffs_from_physics(int n, const double *lambda, double D, double T0, do
 int mdx_coeffs_vjp(int n, const double *lambda, double D, double T0, double rho, double s0,
                    double s1, const double *d_omega2, const double *d_gamma, double *dD,
                    double *dT0, double *ds0, double *ds1, double *d_lambda);
+
+/*
+ * Physical description of one object -> the modal coefficients of an
+ * mdx_instance (host FP64, plan preparation):
+ *   Laplacian eigenpairs, Sec. 3, Eq. 2:
+ *     string (length L)            lambda_mu = (mu pi / L)^2,  mu = 1..N
+ *     rectangle (simply supported)  lambda_mn = (m pi / Lx)^2 + (n pi / Ly)^2,
+ *       the first N by ascending lambda, ties by (m, n), with Lx = sqrt(A / a),
+ *       Ly = sqrt(A a) for area A and aspect a = Ly / Lx;
+ *     unit-norm shapes sqrt(2/L) sin(mu pi x/L), 2/sqrt(Lx Ly) sin(m pi x/Lx) sin(n pi y/Ly)
+ *   omega^2 = (D lambda^2 + T0 lambda) / rho (Eq. 13), gamma = sigma0 + sigma1 omega^2 (Eq. 14)
+ *   b = Phi(x_strike) / rho, c = Phi(x_pickup)   (point force, displacement pickup)
+ *   tau' = EA / (2 L) / rho (string) or E h / (2 Lx Ly (1 - nu^2)) / rho (membrane), Eq. 4
+ *   kappa_k = E / (2 rho_vol zeta_k^4) (plate, Eq. 9)
+ *   stability cut: the modes from the first with omega T >= omega_dt_max on are
+ *   dropped (Stormer-Verlet needs omega T < 2, Eq. 20); a shortened plate keeps
+ *   floor(n_psi N_kept / N) stress modes (at least 1).
+ * The Airy eigenvalues zeta^4 and the coupling tensor H of Eq. 10 come from an
+ * offline FP64 quadrature (the library takes H as an input of mdx_plan_create).
+ */
+#define MDX_SHAPE_STRING 0     /* fixed string of length L */
+#define MDX_SHAPE_RECTANGLE 1  /* simply supported rectangle of area A and aspect a = Ly / Lx */
+
+typedef struct mdx_physics {
+    int kind;              /* MDX_KIND_TENSION (string, membrane) or MDX_KIND_PLATE */
+    int shape;             /* MDX_SHAPE_STRING or MDX_SHAPE_RECTANGLE (plates: rectangle) */
+    int n_phi;             /* transverse modes requested, 1..MDX_MAX_PHI */
+    int n_psi;             /* stress modes requested (plate), 0..MDX_MAX_PSI */
+    double dt;             /* sampling period T > 0 (s) */
+    double omega_dt_max;   /* stability cut on omega T (e.g. 1.9); <= 0 keeps every mode */
+    double length;         /* string length L (m) */
+    double area, aspect;   /* rectangle area A (m^2) and aspect a = Ly / Lx */
+    double D, T0, rho;     /* stiffness, tension, mass per unit length / area (Eq. 13) */
+    double sigma0, sigma1; /* damping gamma = sigma0 + sigma1 omega^2 */
+    double strike[2];      /* strike point relative to L, or to (Lx, Ly) */
+    double pickup[2];      /* pickup point, same convention */
+    double tension_stiffness; /* Eq. 4 numerator: EA (string) or E h / (1 - nu^2) (membrane);
+                                 0 = linear */
+    double vk_scale;       /* E / (2 rho_vol) of Eq. 9 (plate); 0 = linear */
+    const double *zeta4;   /* host [n_psi] Airy eigenvalues zeta^4 (1/m^4), ascending
+                              (nonlinear plate); NULL: kappa is not written, n_psi of
+                              mdx_modal still gives the kept count (the count the
+                              coupling tensor is then computed for) */
+} mdx_physics;
+
+/* Outputs of mdx_modal_from_physics: caller-owned host arrays sized for the
+ * requested counts (n_phi of mdx_physics for the per-mode arrays, n_psi for
+ * kappa); the call writes the kept counts. */
+typedef struct mdx_modal {
+    int n_phi;             /* out: modes kept by the stability cut */
+    int n_psi;             /* out: stress modes kept (0 unless a nonlinear plate) */
+    int *labels;           /* [n_phi][2] (mu, 0) or (m, n); may be NULL */
+    double *lambda, *omega2, *gamma, *b, *c;   /* [n_phi] */
+    double tau;            /* out: tau' (tension kind), else 0 */
+    double *kappa;         /* [n_psi] (nonlinear plate with zeta4), else may be NULL */
+} mdx_modal;
+
+/* Gradients of a scalar loss with respect to the physical parameters. */
+typedef struct mdx_physics_grads {
+    double d_T0, d_D, d_aspect, d_sigma0, d_sigma1;
+    double d_tension_stiffness;   /* through tau' (tension kind) */
+    double d_vk_scale;            /* through kappa (plate) */
+} mdx_physics_grads;
+
+/* Fill `out` from the physical description (see above).  Errors: MDX_ERR_ARG,
+ * MDX_ERR_NONFINITE, MDX_ERR_UNSUPPORTED, MDX_ERR_UNSTABLE (no mode below the
+ * cut). */
+int mdx_modal_from_physics(const mdx_physics *ph, mdx_modal *out);
+
+/*
+ * Vector-Jacobian product of mdx_modal_from_physics (Sec. 4.3: the inverse
+ * problems fit these parameters by gradient descent): maps the per-mode
+ * gradients of mdx_grad back to (T0, D, aspect, sigma0, sigma1) and to the
+ * nonlinear scales (tension_stiffness, vk_scale).
+ *   n_phi, n_psi  the kept counts mdx_modal_from_physics returned
+ *   d_omega2, d_gamma  [n_phi] dL/d omega^2, dL/d gamma
+ *   d_tau    dL/d tau' (tension kind)
+ *   d_kappa  [n_psi] dL/d kappa (plate; may be NULL when n_psi = 0)
+ *   d_dir    <dL/dH, dH/da> of mdx_grad for a plate planned with dH = dH/da
+ *   dzeta4   [n_psi] d zeta^4 / da (plate; NULL = treat zeta^4 as fixed)
+ * With A and the relative strike and pickup points fixed, b, c and a
+ * membrane's tau' do not depend on the aspect; lambda does,
+ *   d lambda_mn / da = (m pi)^2 / A - (n pi)^2 / (A a^2),
+ * and so do kappa (through zeta^4) and H (d_dir).  d_aspect is 0 for strings.
+ * Errors: MDX_ERR_ARG, MDX_ERR_NONFINITE, MDX_ERR_UNSUPPORTED.
+ */
+int mdx_physics_vjp(const mdx_physics *ph, int n_phi, int n_psi, const double *d_omega2,
+                    const double *d_gamma, double d_tau, const double *d_kappa, double d_dir,
+                    const double *dzeta4, mdx_physics_grads *out);
 
 /*
  * Learned proposal network (initial parameter estimates for inverse fitting).
@@ -388,8 +500,8 @@ int mdx_f32_to_bf16(long long n, const float *x, uint16_t *y, void *stream);
  * Scratch: one fixed 1 MiB block of device memory per GPU, owned by the
  * library (a file-scope __device__ array held until the process exits).  It
  * bounds the problem: for n instances, total modes must not exceed
- *   (1048576 - align16(120 n) - align16(4 n) - 176) / 44   (rounded down,
- *   align16(x) = x rounded up to a multiple of 16; 23 824 modes for n = 1);
+ *   (1048576 - align16(120 n) - align16(4 n) - 192) / 48   (rounded down,
+ *   align16(x) = x rounded up to a multiple of 16; 21 838 modes for n = 1);
  * larger requests fail with MDX_ERR_UNSUPPORTED.  No call allocates or frees
  * device memory.  The first call on a device looks up the block's device
  * address (cudaGetSymbolAddress) with that device current; make that first

@@ -29,7 +29,8 @@ EXPORTED = ("mdx_last_error", "mdx_version", "mdx_plan_create", "mdx_plan_destro
             "mdx_plan_tiles", "mdx_simulate_strings_noalloc", "mdx_plan_set_coefficients",
             "mdx_mlp_act_elems", "mdx_mlp_work_elems", "mdx_mlp_forward", "mdx_mlp_backward",
             "mdx_adam_step", "mdx_f32_to_bf16", "mdx_plan_set_l2_keep", "mdx_plan_l2_keep",
-            "mdx_difference_coefficients", "mdx_coefficient_grads")
+            "mdx_difference_coefficients", "mdx_coefficient_grads", "mdx_modal_from_physics",
+            "mdx_physics_vjp")
 
 
 class MdxError(RuntimeError):
@@ -47,14 +48,42 @@ class Instance(ctypes.Structure):
                 ("dt", ctypes.c_double), ("omega2", _D), ("gamma", _D), ("b", _D), ("c", _D),
                 ("lambda_", _D), ("tau", ctypes.c_double), ("H", _F), ("kappa", _D), ("dH", _F),
                 ("phi_class", ctypes.POINTER(ctypes.c_int)),
-                ("psi_class", ctypes.POINTER(ctypes.c_int))]
+                ("psi_class", ctypes.POINTER(ctypes.c_int)), ("geom_group", ctypes.c_int)]
 
 
 class Options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("max_ctas", ctypes.c_int),
                 ("ring_stages", ctypes.c_int), ("stage_bytes", ctypes.c_int),
                 ("force_split", ctypes.c_int), ("wait_limit", ctypes.c_int),
-                ("debug_flags", ctypes.c_int), ("scheme", ctypes.c_int)]
+                ("debug_flags", ctypes.c_int), ("scheme", ctypes.c_int),
+                ("group_engine", ctypes.c_int)]
+
+
+SHAPE_STRING = 0
+SHAPE_RECTANGLE = 1
+
+
+class Physics(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("shape", ctypes.c_int), ("n_phi", ctypes.c_int),
+                ("n_psi", ctypes.c_int), ("dt", ctypes.c_double),
+                ("omega_dt_max", ctypes.c_double), ("length", ctypes.c_double),
+                ("area", ctypes.c_double), ("aspect", ctypes.c_double), ("D", ctypes.c_double),
+                ("T0", ctypes.c_double), ("rho", ctypes.c_double), ("sigma0", ctypes.c_double),
+                ("sigma1", ctypes.c_double), ("strike", ctypes.c_double * 2),
+                ("pickup", ctypes.c_double * 2), ("tension_stiffness", ctypes.c_double),
+                ("vk_scale", ctypes.c_double), ("zeta4", _D)]
+
+
+class Modal(ctypes.Structure):
+    _fields_ = [("n_phi", ctypes.c_int), ("n_psi", ctypes.c_int),
+                ("labels", ctypes.POINTER(ctypes.c_int)), ("lambda_", _D), ("omega2", _D),
+                ("gamma", _D), ("b", _D), ("c", _D), ("tau", ctypes.c_double), ("kappa", _D)]
+
+
+class PhysicsGrads(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("d_T0", "d_D", "d_aspect", "d_sigma0",
+                                                "d_sigma1", "d_tension_stiffness",
+                                                "d_vk_scale")]
 
 
 MLP_MAX_LAYERS = 8
@@ -109,6 +138,10 @@ def load(build_if_missing: bool = True):
         L.mdx_coeffs_vjp.argtypes = [i32, _D, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, _D, _D, _D, _D, _D, _D, _D]
         L.mdx_plan_set_coefficients.argtypes = [vp, _D, _D, _D, _D, _D, _D]
+        L.mdx_modal_from_physics.argtypes = [ctypes.POINTER(Physics), ctypes.POINTER(Modal)]
+        L.mdx_physics_vjp.argtypes = [ctypes.POINTER(Physics), i32, i32, _D, _D,
+                                      ctypes.c_double, _D, ctypes.c_double, _D,
+                                      ctypes.POINTER(PhysicsGrads)]
         L.mdx_difference_coefficients.argtypes = [i32, i32, _D, _D, ctypes.c_double, _D, _D, _D]
         L.mdx_coefficient_grads.argtypes = [i32, i32, _D, _D, ctypes.c_double, _D, _D, _D, _D, _D]
         L.mdx_mlp_act_elems.argtypes = [ctypes.POINTER(MLPDesc), i32]
@@ -170,7 +203,8 @@ class Plan:
     """
 
     def __init__(self, instances, device=0, max_ctas=0, ring_stages=0, stage_bytes=0,
-                 force_split=0, wait_limit=0, debug_flags=0, use_classes=True, scheme="sv"):
+                 force_split=0, wait_limit=0, debug_flags=0, use_classes=True, scheme="sv",
+                 group_engine="tf32x3"):
         L = load()
         self._keep = []
         arr = (Instance * len(instances))()
@@ -214,10 +248,12 @@ class Plan:
                             and use_classes):
                         s.phi_class = iptr(d["phi_class"])
                         s.psi_class = iptr(d["psi_class"])
+                    s.geom_group = int(d.get("geom_group", 0))
                 else:
                     s.n_psi = 0
         opts = Options(device, max_ctas, ring_stages, stage_bytes, force_split, wait_limit,
-                       debug_flags, SCHEMES[scheme] if isinstance(scheme, str) else int(scheme))
+                       debug_flags, SCHEMES[scheme] if isinstance(scheme, str) else int(scheme),
+                       GROUP_ENGINES[group_engine])
         h = ctypes.c_void_p()
         check(L.mdx_plan_create(ctypes.byref(h), arr, len(instances), ctypes.byref(opts)))
         self._h = h
@@ -284,7 +320,8 @@ class Plan:
         check(load().mdx_plan_reset_stats(self._h))
 
     def kernel_stats(self, which):
-        """which: 0 forward, 1 recompute, 2 reverse -> (launches, ms, bytes)."""
+        """which: 0 forward, 1 recompute, 2 reverse, 3 direction contraction,
+        4 fused sweep, 5 grouped plates -> (launches, ms, bytes)."""
         n = ctypes.c_long()
         ms = ctypes.c_double()
         by = ctypes.c_double()
@@ -320,6 +357,7 @@ class Plan:
 
 
 SCHEMES = {"sv": 0, "tf": 1}
+GROUP_ENGINES = {"tf32x3": 0, "off": 1}
 
 
 def difference_coefficients(scheme, omega2, gamma, T):
@@ -364,3 +402,66 @@ def coeffs_vjp(lam, D, T0, rho, s0, s1, d_omega2, d_gamma):
                                 dw.ctypes.data_as(_D), dg.ctypes.data_as(_D),
                                 *[ctypes.byref(o) for o in out], dl.ctypes.data_as(_D)))
     return dict(D=out[0].value, T0=out[1].value, s0=out[2].value, s1=out[3].value, lam=dl)
+
+
+def physics_struct(kind, shape, n_phi, n_psi, dt, omega_dt_max, length=0.0, area=0.0,
+                   aspect=1.0, D=0.0, T0=0.0, rho=1.0, sigma0=0.0, sigma1=0.0,
+                   strike=(0.5, 0.5), pickup=(0.5, 0.5), tension_stiffness=0.0, vk_scale=0.0,
+                   zeta4=None):
+    """mdx_physics of include/mdx.h (zeta4 is kept alive on the returned struct)."""
+    ph = Physics()
+    ph.kind, ph.shape, ph.n_phi, ph.n_psi = int(kind), int(shape), int(n_phi), int(n_psi)
+    ph.dt, ph.omega_dt_max = float(dt), float(omega_dt_max)
+    ph.length, ph.area, ph.aspect = float(length), float(area), float(aspect)
+    ph.D, ph.T0, ph.rho = float(D), float(T0), float(rho)
+    ph.sigma0, ph.sigma1 = float(sigma0), float(sigma1)
+    st = list(strike) + [0.0] * (2 - len(strike))
+    pk = list(pickup) + [0.0] * (2 - len(pickup))
+    ph.strike[0], ph.strike[1] = float(st[0]), float(st[1])
+    ph.pickup[0], ph.pickup[1] = float(pk[0]), float(pk[1])
+    ph.tension_stiffness, ph.vk_scale = float(tension_stiffness), float(vk_scale)
+    if zeta4 is not None:
+        z = np.ascontiguousarray(zeta4, dtype=np.float64)
+        ph._zeta4 = z
+        ph.zeta4 = z.ctypes.data_as(_D)
+    return ph
+
+
+def modal_from_physics(ph):
+    """mdx_modal_from_physics: dict of labels, lam, omega2, gamma, b, c, tau,
+    kappa (kept modes only)."""
+    n, m = ph.n_phi, max(ph.n_psi, 1)
+    labels = np.zeros((n, 2), np.int32)
+    arrs = {k: np.zeros(n) for k in ("lam", "omega2", "gamma", "b", "c")}
+    kappa = np.zeros(m)
+    out = Modal()
+    out.labels = labels.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    out.lambda_, out.omega2, out.gamma, out.b, out.c = (
+        arrs[k].ctypes.data_as(_D) for k in ("lam", "omega2", "gamma", "b", "c"))
+    out.kappa = kappa.ctypes.data_as(_D)
+    check(load().mdx_modal_from_physics(ctypes.byref(ph), ctypes.byref(out)))
+    ne, me = out.n_phi, out.n_psi
+    res = {k: v[:ne].copy() for k, v in arrs.items()}
+    res["labels"] = labels[:ne].astype(np.int64)
+    res["tau"] = out.tau
+    res["kappa"] = kappa[:me].copy()
+    res["n_psi"] = me
+    return res
+
+
+def physics_vjp(ph, n_phi, n_psi, d_omega2, d_gamma, d_tau=0.0, d_kappa=None, d_dir=0.0,
+                dzeta4=None):
+    """mdx_physics_vjp: dict of d_T0, d_D, d_aspect, d_sigma0, d_sigma1,
+    d_tension_stiffness, d_vk_scale."""
+    dw = np.ascontiguousarray(d_omega2, dtype=np.float64)
+    dg = np.ascontiguousarray(d_gamma, dtype=np.float64)
+    dk = None if d_kappa is None else np.ascontiguousarray(d_kappa, dtype=np.float64)
+    dz = None if dzeta4 is None else np.ascontiguousarray(dzeta4, dtype=np.float64)
+    out = PhysicsGrads()
+    check(load().mdx_physics_vjp(ctypes.byref(ph), int(n_phi), int(n_psi), dw.ctypes.data_as(_D),
+                                 dg.ctypes.data_as(_D), float(d_tau),
+                                 dk.ctypes.data_as(_D) if dk is not None else None,
+                                 float(d_dir),
+                                 dz.ctypes.data_as(_D) if dz is not None else None,
+                                 ctypes.byref(out)))
+    return {k: getattr(out, k) for k, _ in PhysicsGrads._fields_}

@@ -28,6 +28,43 @@ __device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
     sum = t;
 }
 
+// Compensated pickup term: (s, e) += (c + c_lo) (q_hi + q_lo).  The product c q_hi is
+// split exactly (its rounding error from an fma), the sum is a two-sum, and
+// the small terms (product error, c q_lo, sum error) gather in e.  The pickup
+// sum y = sum_mu c_mu q_mu can cancel strongly (a pickup near nodal lines of
+// the dominant modes), so plain FP32 summation of the rounded q_hi would lose
+// digits that the compensated state still holds.
+__device__ __forceinline__ void pickup_add(float &s, float &e, float c, float clo, float qhi,
+                                           float qlo) {
+    const float p = c * qhi;
+    const float pe = fmaf(c, qhi, -p);
+    const float t = s + p;
+    const float bb = t - s;
+    const float err = (s - (t - bb)) + (p - bb);
+    s = t;
+    e += err + fmaf(c, qlo, fmaf(clo, qhi, pe));
+}
+
+// (s, e) += (s2, e2) with the sum's rounding error folded into e.
+__device__ __forceinline__ void pickup_merge(float &s, float &e, float s2, float e2) {
+    const float t = s + s2;
+    const float bb = t - s;
+    const float err = (s - (t - bb)) + (s2 - bb);
+    s = t;
+    e += e2 + err;
+}
+
+// Compensated warp reduction of (s, e); every lane receives the total s + e.
+__device__ __forceinline__ float warp_pickup_sum(float s, float e) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+        const float e2 = __shfl_xor_sync(0xffffffffu, e, o);
+        pickup_merge(s, e, s2, e2);
+    }
+    return s + e;
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -14,8 +14,11 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include <cuda_runtime.h>
+
+#include "../../include/mdx.h"
 
 namespace mdx {
 
@@ -49,6 +52,7 @@ struct ModeCoef {
     const float *b;     // input weight
     const float *c;     // pickup weight
     const float *lam;   // Laplacian eigenvalue (tension kind)
+    const float *clo;   // c - (float)c (low part of the pickup weight)
 };
 
 struct InstDesc {
@@ -63,6 +67,7 @@ struct InstDesc {
     int n_contrib;      // plate: number of CTAs holding a part of the k range
     long long part_off; // plate: first exchange slot (slots are [n_contrib][3][Npad])
     int has_dir;        // plate: a direction tensor dH is present
+    int grouped;        // plate: simulated by the grouped kernel (shared coupling tensor)
     long long dH_off;   // float offset of dH^0 (same layout as H)
     // symmetry-class layout (parity != 0): transverse modes in class order
     int parity;
@@ -229,6 +234,97 @@ struct TensionParams {
     float *tacc;                  // [n_inst][2] d tau' (Kahan sum, compensation)
     int *status;
 };
+
+// ---------------------------------------------------------------- grouped plates
+// Plates that share one coupling tensor (same geometry: their modes are
+// prefixes of the largest member's, Sec. 3, Eq. 2 and Eq. 10) are stepped
+// together: per step and stress mode k, U^k = H^k [q_1 ... q_B] is one
+// tensor-core GEMM over the plates of the group (split TF32 on tcgen05, FP32
+// accumulation in tensor memory), see mdx_group.cu.
+constexpr int kGrpThreads = 256;      // 8 warps: producer, MMA, 2 converters, 4 epilogue
+constexpr int kGrpChunk = 16;         // K elements (columns of H^k) per ring stage
+constexpr int kGrpStageBytes = 128 * kGrpChunk * 4;   // one 128-row stage (8 KB)
+constexpr int kGrpMaxTiles = 16;      // (row class, 128-row tile) blocks per stress mode
+constexpr int kGrpMaxB = 64;          // plates per kernel group
+
+// One kernel group: up to kGrpMaxB plates stepped together on one coupling image.
+struct GrpDesc {
+    int B, Bp;              // plates, padded to a multiple of 16 (the MMA's N)
+    int N, M;               // transverse / stress modes of the image (largest member)
+    int Np;                 // row stride of the class-ordered buffers (N rounded up to 4)
+    int ncls[4], ocls[4];   // transverse modes per class, class-order offset of each class
+    int kpad[4];            // class sizes rounded up to kGrpChunk (K of the MMAs)
+    int n_tiles;
+    int tile_sb[kGrpMaxTiles];    // row class of each tile
+    int tile_r0[kGrpMaxTiles];    // first row within the class
+    int tile_rows[kGrpMaxTiles];  // rows (<= 128)
+    int cta0, n_ctas;       // CTAs [cta0, cta0 + n_ctas) hold this group's stress modes
+    int plate0;             // plates: GroupParams::plates[plate0 .. plate0 + B)
+    int qoff[4];            // shared-memory float offset of class a's Q image [Bp][kpad[a]]
+                            // (its low part follows at qoff[a] + Bp * kpad[a])
+    long long gpos_off;     // gpos[gpos_off + j] = class position of mode j
+    long long kap_off;      // kappa table [units of the group][Bp], 0 where a plate lacks the mode
+    long long part_off;     // partial forces [n_ctas][Bp][Np] (class order)
+    long long qbuf_off;     // current q_hi [Bp][Np] (class order), written by the owners
+};
+
+// One stress mode of a kernel group (the MMA and epilogue work unit).
+struct GrpUnit {
+    int g;                  // kernel group
+    int row;                // row of the group's kappa table
+    int c;                  // symmetry class of the stress mode
+    int pad;
+    long long off[kGrpMaxTiles];   // float offset of each tile's image (-1: empty block)
+};
+
+struct GrpPlate {
+    int inst;               // instance index
+    int owner;              // CTA that steps this plate's state
+};
+
+struct GroupParams {
+    const InstDesc *inst;
+    const GrpDesc *groups;
+    const GrpUnit *units;
+    const int *cta_group;         // [grid] kernel group of each CTA
+    const int *cta_units;         // [grid][2] unit range of each CTA
+    const GrpPlate *plates;
+    const int *gpos;
+    const float *kap;
+    const float *img;             // coupling images (tile chunks, see mdx_group.cu)
+    float *part, *qbuf;
+    ModeCoef coef;
+    int steps, n_begin, total_steps;
+    const float *exc;
+    float *audio;
+    float *state_io;              // [4][total_modes]
+    long long total_modes;
+    unsigned *counters;           // [kernel groups]
+    int *status;
+    int *abort_flag;
+    long long wait_limit;
+    int ring_stages;
+    int ring_off, lo_off, q_off, scratch_off;   // shared-memory byte offsets
+    float l2_keep;
+};
+
+struct GroupPlan;   // host side of the grouped path (mdx_group.cu)
+// Builds the grouped path for the plates with grouped[i] != 0 (host FP32 H,
+// classes and kappa from the instance descriptions); fails with an MDX_ERR_*.
+int group_plan_build(GroupPlan **out, const mdx_instance *I, const std::vector<InstDesc> &inst,
+                     const std::vector<int> &grouped, int device, int n_sms, int smem_optin,
+                     long long wait_limit);
+void group_plan_free(GroupPlan *g);
+int group_plan_ctas(const GroupPlan *g);
+double group_plan_bytes_per_step(const GroupPlan *g);
+double group_plan_flops_per_step(const GroupPlan *g);
+// kappa of every plate (user order, concatenated over all instances' stress modes)
+int group_plan_set_kappa(GroupPlan *g, const std::vector<InstDesc> &inst,
+                         const std::vector<double> &kappa_user);
+cudaError_t group_plan_launch(GroupPlan *g, const InstDesc *d_inst, const ModeCoef &coef,
+                              int steps, int total_steps, const float *exc, float *audio,
+                              float *state_io, long long total_modes, int *status, int *abort_flag,
+                              float l2_keep, cudaStream_t s);
 
 // Sets the thread-local message returned by mdx_last_error; returns code.
 int set_last_error(int code, const char *msg);

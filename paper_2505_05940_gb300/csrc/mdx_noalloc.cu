@@ -79,8 +79,8 @@ static long noalloc_max_modes(int n_inst) {
     if (n_inst < 1) return 0;
     const size_t head = align16((size_t)n_inst * sizeof(InstDesc)) + align16((size_t)n_inst * sizeof(int));
     if (head >= kNoAllocBytes) return 0;
-    // 7 coefficient arrays + 4 state arrays, each 16-byte aligned
-    return (long)((kNoAllocBytes - head - 11 * 16) / (11 * sizeof(float)));
+    // 8 coefficient arrays + 4 state arrays, each 16-byte aligned
+    return (long)((kNoAllocBytes - head - 12 * 16) / (12 * sizeof(float)));
 }
 
 extern "C" int mdx_simulate_strings_noalloc(const mdx_instance *inst, int n_inst, const float *exc,
@@ -117,7 +117,7 @@ extern "C" int mdx_simulate_strings_noalloc(const mdx_instance *inst, int n_inst
         return noalloc_fail(MDX_ERR_UNSUPPORTED,
                             "total modes exceed the fixed 1 MiB scratch block of the "
                             "no-allocation entry point (at most (1048576 - align16(120 n) - "
-                            "align16(4 n) - 176) / 44 for n instances)");
+                            "align16(4 n) - 192) / 48 for n instances)");
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
@@ -140,7 +140,7 @@ extern "C" int mdx_simulate_strings_noalloc(const mdx_instance *inst, int n_inst
     const size_t off_list = align16(n_inst * sizeof(InstDesc));
     const size_t off_coef = off_list + align16(n_inst * sizeof(int));
     const size_t coef_stride = align16(TM * sizeof(float));
-    const size_t off_state = off_coef + 7 * coef_stride;
+    const size_t off_state = off_coef + 8 * coef_stride;
     std::vector<unsigned char> img(off_state, 0);
     InstDesc *desc = reinterpret_cast<InstDesc *>(img.data());
     int *list = reinterpret_cast<int *>(img.data() + off_list);
@@ -168,6 +168,7 @@ extern "C" int mdx_simulate_strings_noalloc(const mdx_instance *inst, int n_inst
             cf[4 * cs + mo + m] = (float)I.c[m];
             cf[5 * cs + mo + m] = (float)I.lambda[m];
             cf[6 * cs + mo + m] = k.rho_lo;
+            cf[7 * cs + mo + m] = (float)(I.c[m] - (double)(float)I.c[m]);
         }
         mo += I.n_phi;
     }
@@ -207,6 +208,7 @@ extern "C" int mdx_simulate_strings_noalloc(const mdx_instance *inst, int n_inst
         T.coef.c = dcf + 4 * cs;
         T.coef.lam = dcf + 5 * cs;
         T.coef.rw2lo = dcf + 6 * cs;
+        T.coef.clo = dcf + 7 * cs;
         T.steps = steps;
         T.n_begin = 0;
         T.total_steps = steps;

@@ -101,8 +101,8 @@ struct mdx_plan {
         cudaEvent_t a, b;
     };
     std::vector<Rec> recs;
-    long stat_launch[5] = {0, 0, 0, 0, 0};
-    double stat_ms[5] = {0, 0, 0, 0, 0}, stat_bytes[5] = {0, 0, 0, 0, 0};
+    long stat_launch[6] = {0, 0, 0, 0, 0, 0};
+    double stat_ms[6] = {0, 0, 0, 0, 0, 0}, stat_bytes[6] = {0, 0, 0, 0, 0, 0};
     double H_bytes_per_step = 0, dH_bytes_per_step = 0;
     int smem_optin = 0;
     // L2 residency of the coupling stream: requested fraction (< 0: automatic)
@@ -122,8 +122,12 @@ struct mdx_plan {
     int n_dir_groups = 0;
     // host copies for coefficient updates
     std::vector<double> h_omega2, h_gamma, h_b, h_c, h_tau, h_kappa;
-    std::vector<int> h_kperm;      // internal stress index -> user index, concatenated
-    float *d_coef_all = nullptr;   // the 7 FP32 coefficient arrays
+    std::vector<int> h_kperm;      // internal stress index -> user index, at each k_off
+    float *d_coef_all = nullptr;   // the 8 FP32 coefficient arrays
+    // plates sharing a coupling tensor, stepped by the grouped tensor-core kernel
+    GroupPlan *grp = nullptr;
+    std::vector<int> grouped;      // per instance
+    bool any_grouped = false;
 };
 
 namespace {
@@ -244,6 +248,7 @@ int mdx_plan_destroy(mdx_plan *p) {
         cudaEventDestroy(r.b);
     }
     for (void *a : p->allocs) cudaFree(a);
+    group_plan_free(p->grp);
     if (prev >= 0) cudaSetDevice(prev);
     delete p;
     return MDX_OK;
@@ -283,7 +288,7 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
     };
 
     // ---- per-instance layout and FP64 -> FP32 coefficients (difference form)
-    std::vector<float> eps, rw2, rw2lo, r, b, c, lam;
+    std::vector<float> eps, rw2, rw2lo, r, b, c, lam, clo;
     std::vector<double> w2d, gmd, dtd;
     p->inst.resize(n_inst);
     p->dt.resize(n_inst);
@@ -310,6 +315,7 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
             r.push_back(k.r);
             b.push_back((float)S.b[m]);
             c.push_back((float)S.c[m]);
+            clo.push_back((float)(S.c[m] - (double)(float)S.c[m]));
             lam.push_back(S.kind == MDX_KIND_TENSION ? (float)S.lambda[m] : 0.f);
             w2d.push_back(S.omega2[m]);
             gmd.push_back(S.gamma[m]);
@@ -318,6 +324,22 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
         p->inst[i] = d;
     }
     const size_t TM = (size_t)p->total_modes;
+    // Plates of one geometry group (geom_group > 0) are stepped by the grouped
+    // tensor-core kernel unless the options ask for per-instance copies; the
+    // per-instance machinery below sees them as plates without stress modes.
+    p->grouped.assign(n_inst, 0);
+    if (o.group_engine != MDX_GROUP_OFF) {
+        for (int i = 0; i < n_inst; ++i) {
+            InstDesc &d = p->inst[i];
+            if (d.kind == MDX_KIND_PLATE && d.M > 0 && I[i].geom_group > 0) {
+                p->grouped[i] = 1;
+                p->any_grouped = true;
+                d.grouped = 1;
+                d.M = 0;
+                d.has_dir = 0;
+            }
+        }
+    }
     for (int i = 0; i < n_inst; ++i) {
         const mdx_instance &S = I[i];
         for (int m = 0; m < S.n_phi; ++m) {
@@ -332,8 +354,9 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
     p->h_gamma = gmd;
     {
         std::vector<float> all;
-        all.reserve(7 * TM);
-        for (auto *v : {&eps, &rw2, &r, &b, &c, &lam, &rw2lo}) all.insert(all.end(), v->begin(), v->end());
+        all.reserve(8 * TM);
+        for (auto *v : {&eps, &rw2, &r, &b, &c, &lam, &rw2lo, &clo})
+            all.insert(all.end(), v->begin(), v->end());
         float *dc = nullptr;
         int rc = upload(p, &dc, all.data(), all.size());
         if (rc) return bail(rc);
@@ -345,6 +368,7 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
         p->coef.c = dc + 4 * TM;
         p->coef.lam = dc + 5 * TM;
         p->coef.rw2lo = dc + 6 * TM;
+        p->coef.clo = dc + 7 * TM;
         if ((rc = upload(p, &p->d_omega2, w2d.data(), TM))) return bail(rc);
         if ((rc = upload(p, &p->d_gamma, gmd.data(), TM))) return bail(rc);
         if ((rc = upload(p, &p->d_dt, dtd.data(), TM))) return bail(rc);
@@ -352,6 +376,7 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
     // ---- tension list (strings, membranes and plates without coupling)
     for (int i = 0; i < n_inst; ++i) {
         const InstDesc &d = p->inst[i];
+        if (d.grouped) continue;
         if (d.kind == MDX_KIND_TENSION || d.M == 0) {
             p->tension.push_back(i);
             p->tension_max_n = std::max(p->tension_max_n, d.N);
@@ -762,15 +787,19 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
                 if (d.has_dir) p->dH_bytes_per_step += per_step;
             }
             // kappa in internal (class-sorted) order, class permutations
-            std::vector<float> kap2;
-            std::vector<int> perm_all, kperm_all;
+            // indexed by each plate's k_off (grouped plates keep their range, unused here)
+            std::vector<float> kap2(std::max<long long>(p->total_k, 1), 0.f);
+            std::vector<int> perm_all, kperm_all(std::max<long long>(p->total_k, 1), 0);
+            p->h_kperm.assign(std::max<long long>(p->total_k, 1), 0);
             for (int i = 0; i < n_inst; ++i) {
                 InstDesc &d = p->inst[i];
-                for (int kk = 0; kk < d.M; ++kk) p->h_kperm.push_back(kperm[i][kk]);
-                for (int kk = 0; kk < d.M; ++kk) kap2.push_back((float)I[i].kappa[kperm[i][kk]]);
+                for (int kk = 0; kk < d.M; ++kk) {
+                    p->h_kperm[d.k_off + kk] = kperm[i][kk];
+                    kap2[d.k_off + kk] = (float)I[i].kappa[kperm[i][kk]];
+                    kperm_all[d.k_off + kk] = kperm[i][kk];
+                }
                 d.perm_off = (long long)perm_all.size();
                 for (int v : perm[i]) perm_all.push_back(v);
-                for (int kk = 0; kk < d.M; ++kk) kperm_all.push_back(kperm[i][kk]);
             }
             if ((rc2 = upload(p, &p->d_kappa, kap2.data(), kap2.size()))) return bail(rc2);
             if ((rc2 = upload(p, &p->d_perm, perm_all.data(), perm_all.size()))) return bail(rc2);
@@ -857,6 +886,17 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
         if ((rc = dalloc(p, reinterpret_cast<void **>(&p->d_part), 2 * p->part_stride * sizeof(float)))) return bail(rc);
     }
     int rc;
+    if (p->any_grouped) {
+        int dev_sms = 0, smem_optin = 0;
+        MDX_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, p->device), "attr");
+        MDX_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device), "attr");
+        if (o.max_ctas > 0) dev_sms = std::min(dev_sms, o.max_ctas);
+        if ((rc = group_plan_build(&p->grp, I, p->inst, p->grouped, p->device, dev_sms,
+                                   smem_optin - 2048, p->wait_limit)))
+            return bail(rc);
+        if ((rc = group_plan_set_kappa(p->grp, p->inst, p->h_kappa))) return bail(rc);
+        if (!p->d_abort && (rc = dalloc(p, reinterpret_cast<void **>(&p->d_abort), 16))) return bail(rc);
+    }
     if ((rc = upload(p, &p->d_inst, p->inst.data(), p->inst.size()))) return bail(rc);
     if ((rc = upload(p, &p->d_tension, p->tension.data(), p->tension.size()))) return bail(rc);
     if ((rc = dalloc(p, reinterpret_cast<void **>(&p->d_counters), n_inst * sizeof(unsigned)))) return bail(rc);
@@ -1023,9 +1063,32 @@ int run_plate(mdx_plan *p, PlateParams &P, cudaStream_t s) {
     return MDX_OK;
 }
 
+int run_grouped(mdx_plan *p, const PlateParams &P, cudaStream_t s) {
+    if (!p->grp) return MDX_OK;
+    MDX_CUDA(cudaMemsetAsync(p->d_abort, 0, sizeof(int), s), "memset");
+    mdx_plan::Rec rec{};
+    if (p->profiling) {
+        rec.which = 5;
+        rec.bytes = (double)P.steps * group_plan_bytes_per_step(p->grp);
+        MDX_CUDA(cudaEventCreate(&rec.a), "event");
+        MDX_CUDA(cudaEventCreate(&rec.b), "event");
+        MDX_CUDA(cudaEventRecord(rec.a, s), "event");
+    }
+    MDX_CUDA(group_plan_launch(p->grp, p->d_inst, p->coef, P.steps, P.total_steps, P.exc, P.audio,
+                               P.state_io, p->total_modes, P.status, p->d_abort, p->l2_keep, s),
+             "grouped plate kernel");
+    if (p->profiling) {
+        MDX_CUDA(cudaEventRecord(rec.b, s), "event");
+        p->recs.push_back(rec);
+    }
+    return MDX_OK;
+}
+
 int run_segment(mdx_plan *p, PlateParams &P, TensionParams &T, cudaStream_t s) {
     if (!p->tension.empty()) MDX_CUDA(launch_tension(T, p->tension_max_n, s), "tension kernel");
-    return run_plate(p, P, s);
+    const int rc = run_plate(p, P, s);
+    if (rc) return rc;
+    return run_grouped(p, P, s);
 }
 
 }  // namespace
@@ -1036,6 +1099,10 @@ extern "C" int mdx_simulate(mdx_plan *p, const float *exc, const double *q0, con
     if (!p) return fail(MDX_ERR_ARG, "plan is NULL");
     if (steps < 0) return fail(MDX_ERR_ARG, "steps must be >= 0");
     if (ckpt && K <= 0) return fail(MDX_ERR_ARG, "checkpoint interval K must be > 0");
+    if (ckpt && p->any_grouped)
+        return fail(MDX_ERR_UNSUPPORTED,
+                    "checkpoints (and mdx_grad) need per-instance coupling tensors: plan grouped "
+                    "plates with group_engine = MDX_GROUP_OFF");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     MDX_CUDA(cudaSetDevice(p->device), "cudaSetDevice");
     if (status) MDX_CUDA(cudaMemsetAsync(status, 0, p->n_inst * sizeof(int), s), "memset status");
@@ -1105,6 +1172,10 @@ extern "C" int mdx_grad(mdx_plan *p, const float *exc, const double *q0, const d
                         int steps, const float *d_audio, int K, const void *ckpt, void *work,
                         size_t work_bytes, const mdx_grads *out, int *status, void *stream) {
     if (!p) return fail(MDX_ERR_ARG, "plan is NULL");
+    if (p->any_grouped)
+        return fail(MDX_ERR_UNSUPPORTED,
+                    "mdx_grad needs per-instance coupling tensors: plan grouped plates with "
+                    "group_engine = MDX_GROUP_OFF");
     if (steps <= 0) return fail(MDX_ERR_ARG, "steps must be > 0");
     if (K <= 0 || !ckpt) return fail(MDX_ERR_ARG, "mdx_grad needs the checkpoints of mdx_simulate (K > 0)");
     if (!d_audio) return fail(MDX_ERR_ARG, "d_audio is required");
@@ -1342,14 +1413,14 @@ extern "C" int mdx_plan_reset_stats(mdx_plan *p) {
         cudaEventDestroy(r.b);
     }
     p->recs.clear();
-    for (int i = 0; i < 5; ++i) p->stat_launch[i] = 0, p->stat_ms[i] = 0, p->stat_bytes[i] = 0;
+    for (int i = 0; i < 6; ++i) p->stat_launch[i] = 0, p->stat_ms[i] = 0, p->stat_bytes[i] = 0;
     return MDX_OK;
 }
 
 extern "C" int mdx_plan_kernel_stats(mdx_plan *p, int which, long *launches, double *ms,
                                      double *bytes) {
     if (!p) return fail(MDX_ERR_ARG, "plan is NULL");
-    if (which < 0 || which > 4) return fail(MDX_ERR_ARG, "which must be 0..4");
+    if (which < 0 || which > 5) return fail(MDX_ERR_ARG, "which must be 0..5");
     for (auto &r : p->recs) {
         MDX_CUDA(cudaEventSynchronize(r.b), "event sync");
         float t = 0.f;
@@ -1421,7 +1492,7 @@ extern "C" int mdx_plan_set_coefficients(mdx_plan *p, const double *omega2, cons
     }
     for (double v : kp)
         if (!std::isfinite(v)) return fail(MDX_ERR_NONFINITE, "non-finite kappa");
-    std::vector<float> eps(TM), rw2(TM), rr(TM), bf(TM), cf(TM), rwl(TM);
+    std::vector<float> eps(TM), rw2(TM), rr(TM), bf(TM), cf(TM), rwl(TM), cl(TM);
     for (int i = 0; i < p->n_inst; ++i) {
         const InstDesc &d = p->inst[i];
         const double T = p->dt[i];
@@ -1434,6 +1505,7 @@ extern "C" int mdx_plan_set_coefficients(mdx_plan *p, const double *omega2, cons
             rr[g] = k.r;
             bf[g] = (float)bb[g];
             cf[g] = (float)cc[g];
+            cl[g] = (float)(cc[g] - (double)cf[g]);
         }
     }
     MDX_CUDA(cudaSetDevice(p->device), "cudaSetDevice");
@@ -1445,6 +1517,7 @@ extern "C" int mdx_plan_set_coefficients(mdx_plan *p, const double *omega2, cons
     MDX_CUDA(cudaMemcpy(dc + 3 * TM, bf.data(), TM * 4, cudaMemcpyHostToDevice), "upload");
     MDX_CUDA(cudaMemcpy(dc + 4 * TM, cf.data(), TM * 4, cudaMemcpyHostToDevice), "upload");
     MDX_CUDA(cudaMemcpy(dc + 6 * TM, rwl.data(), TM * 4, cudaMemcpyHostToDevice), "upload");
+    MDX_CUDA(cudaMemcpy(dc + 7 * TM, cl.data(), TM * 4, cudaMemcpyHostToDevice), "upload");
     MDX_CUDA(cudaMemcpy(p->d_omega2, w2.data(), TM * 8, cudaMemcpyHostToDevice), "upload");
     MDX_CUDA(cudaMemcpy(p->d_gamma, gm.data(), TM * 8, cudaMemcpyHostToDevice), "upload");
     // tau lives in the instance table; kappa in internal (class-sorted) order
@@ -1460,6 +1533,10 @@ extern "C" int mdx_plan_set_coefficients(mdx_plan *p, const double *omega2, cons
             }
         }
         MDX_CUDA(cudaMemcpy(p->d_kappa, k2.data(), p->total_k * 4, cudaMemcpyHostToDevice), "upload");
+    }
+    if (p->grp) {
+        const int rc = group_plan_set_kappa(p->grp, p->inst, kp);
+        if (rc) return rc;
     }
     p->h_omega2 = w2;
     p->h_gamma = gm;

@@ -825,7 +825,7 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
             const float e = (P.exc && rev_on) ? P.exc[(long long)item.inst * P.total_steps + n] : 0.f;
             const float e_rec =
                 (FUSED && P.exc) ? P.exc[(long long)item.inst * P.total_steps + P.rec_begin + it] : 0.f;
-            float yp = 0.f;
+            float ys = 0.f, ye = 0.f;   // compensated pickup (owner)
             for (int s = tid; s < d.N; s += kPlateThreads) {
                 const long long m = d.mode_off + s;
                 float fA, fB = 0.f, fR = 0.f;
@@ -844,12 +844,12 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                 }
                 const float eps = P.coef.eps[m], rw2 = P.coef.rw2[m], r = P.coef.r[m];
                 const float rw2l = P.coef.rw2lo[m];
-                const float b = P.coef.b[m], c = P.coef.c[m];
+                const float b = P.coef.b[m], c = P.coef.c[m], clo = P.coef.clo[m];
                 float x0 = st[ST_QHI * Np + s], x1 = st[ST_QLO * Np + s], x2 = st[ST_V * Np + s];
                 float x3 = st[ST_VLO * Np + s];
                 if (!reverse) {
                     sv_step(x0, x1, x2, x3, eps, rw2, rw2l, r, fmaf(b, e, -fA));
-                    yp = fmaf(c, x0, yp);
+                    pickup_add(ys, ye, c, clo, x0, x1);
                 } else if (rev_on) {
                     // fA = J w (summed), fB = fnl(q^n)
                     if (item.owner) {
@@ -894,14 +894,23 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
             }
             if (!reverse) {
                 // pickup y^n (owner) ; reduction buffer alternates so one barrier suffices
-                yp = warp_sum(yp);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float s2 = __shfl_xor_sync(0xffffffffu, ys, o);
+                    const float e2 = __shfl_xor_sync(0xffffffffu, ye, o);
+                    pickup_merge(ys, ye, s2, e2);
+                }
                 float *r2 = S.red2 + red2_parity * 2 * kPlateWarps;
-                if (lane == 0) r2[warp] = yp;
+                if (lane == 0) {
+                    r2[warp] = ys;
+                    r2[kPlateWarps + warp] = ye;
+                }
                 consumer_bar();
                 if (tid == 0 && item.owner) {
-                    float y = 0.f;
+                    float y = 0.f, ycomp = 0.f;
 #pragma unroll
-                    for (int w = 0; w < kPlateWarps; ++w) y += r2[w];
+                    for (int w = 0; w < kPlateWarps; ++w) pickup_merge(y, ycomp, r2[w], r2[kPlateWarps + w]);
+                    y += ycomp;
                     if (P.mode == MODE_FORWARD && P.audio)
                         P.audio[(long long)item.inst * P.total_steps + n] = y;
                     if (!isfinite(y)) set_status(P.status, item.inst, MDX_ERR_NONFINITE);

@@ -29,7 +29,7 @@ tension_kernel(const TensionParams P) {
     const long long TM = P.total_modes;
     const float taup = d.taup;
 
-    float eps[J], rw2[J], rw2l[J], r[J], b[J], c[J], lam[J];
+    float eps[J], rw2[J], rw2l[J], r[J], b[J], c[J], clo[J], lam[J];
     float x0[J], x1[J], x2[J], x3[J];   // forward: q_hi, q_lo, v_hi, v_lo ; reverse: a_hi, a_lo, mu
 #pragma unroll
     for (int j = 0; j < J; ++j) {
@@ -41,6 +41,7 @@ tension_kernel(const TensionParams P) {
         r[j] = ok ? P.coef.r[mo + m] : 0.f;
         b[j] = ok ? P.coef.b[mo + m] : 0.f;
         c[j] = ok ? P.coef.c[mo + m] : 0.f;
+        clo[j] = ok ? P.coef.clo[mo + m] : 0.f;
         lam[j] = ok ? P.coef.lam[mo + m] : 0.f;
     }
     const float *exc = P.exc ? P.exc + (long long)inst * P.total_steps : nullptr;
@@ -95,19 +96,22 @@ tension_kernel(const TensionParams P) {
                     }
                 }
             }
-            float yp = 0.f, Sp = 0.f;
+            float ys = 0.f, ye = 0.f, Sp = 0.f;
 #pragma unroll
             for (int j = 0; j < J; ++j) {
                 const float f = taup * lam[j] * x0[j] * S;
                 sv_step(x0[j], x1[j], x2[j], x3[j], eps[j], rw2[j], rw2l[j], r[j], fmaf(b[j], e, -f));
-                yp = fmaf(c[j], x0[j], yp);
+                pickup_add(ys, ye, c[j], clo[j], x0[j], x1[j]);
                 Sp = fmaf(lam[j] * x0[j], x0[j], Sp);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                yp += __shfl_xor_sync(0xffffffffu, yp, o);
+                const float s2 = __shfl_xor_sync(0xffffffffu, ys, o);
+                const float e2 = __shfl_xor_sync(0xffffffffu, ye, o);
+                pickup_merge(ys, ye, s2, e2);
                 Sp += __shfl_xor_sync(0xffffffffu, Sp, o);
             }
+            const float yp = ys + ye;
             S = Sp;
             if (lane == (it & 31)) ybuf = yp;
             if (!isfinite(yp)) bad = true;

@@ -161,7 +161,8 @@ def _aspect_bank(grid, n_phi=200, n_psi=50, area=W.PLATE_AREA):
     bank = {}
     for a in grid:
         Lx, Ly = coupling.sides(area, a)
-        labels, _ = physics.rectangle_eigen(Lx, Ly, n_phi)
+        labels = physics.mode_labels(W.Instance(kind="plate", n_phi=n_phi, aspect=float(a),
+                                                area=area), n_phi)
         airy = coupling.airy_modes(Lx, Ly, n_psi)
         H, z = coupling.coupling_tensor(Lx, Ly, labels, n_psi, airy=airy)
         bank[float(a)] = (labels, H.astype(np.float32), z, coupling.airy_classes(airy[1]))

@@ -31,12 +31,27 @@ def test_defaults_finish_within_minutes():
     assert (a.n_inst, a.n_phi, a.n_psi, a.sim_steps, a.K) == (64, 200, 50, 22050, 1024)
 
 
-def test_profiled_traffic_follows_the_kernel_source():
+def test_profiled_traffic_follows_the_kernel_source(tmp_path, monkeypatch):
+    """The traffic figure is read from the committed ncu summary only while the
+    kernel source still has the hash recorded there; after a kernel edit it
+    is null until the kernel is profiled again."""
+    import hashlib
     b = _bench()
     a = types.SimpleNamespace(n_inst=64, n_phi=200, n_psi=50)
-    t = b.profiled_traffic(a, 1024)
-    # the committed summary matches the current plate kernel source
-    assert t is not None and 5e10 < t < 1.4e11
+    src = os.path.join(ROOT, "paper_2505_05940_gb300", "csrc", "mdx_plate.cu")
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    root = tmp_path / "r"
+    (root / "profiles").mkdir(parents=True)
+    (root / "paper_2505_05940_gb300" / "csrc").mkdir(parents=True)
+    (root / "paper_2505_05940_gb300" / "csrc" / "mdx_plate.cu").write_bytes(open(src, "rb").read())
+    summary = root / "profiles" / "plate_kernel_fused_64plates_200x50.md"
+    summary.write_text("kernel-source: paper_2505_05940_gb300/csrc/mdx_plate.cu sha256 "
+                       f"{digest}\ntraffic_bytes_per_step: 75827031\n")
+    monkeypatch.setattr(b, "ROOT", str(root))
+    assert b.profiled_traffic(a, 1024) == 75827031 * 1024
+    summary.write_text("kernel-source: paper_2505_05940_gb300/csrc/mdx_plate.cu sha256 "
+                       "0123456789abcdef\ntraffic_bytes_per_step: 75827031\n")
+    assert b.profiled_traffic(a, 1024) is None
     # another workload has no captured traffic
     assert b.profiled_traffic(types.SimpleNamespace(n_inst=32, n_phi=200, n_psi=50), 1024) is None
 

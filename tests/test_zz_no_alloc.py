@@ -11,8 +11,9 @@ coefficients, so the results must be identical bit for bit:
     first call's contents);
   * with the optional inputs left out (zero initial state, no excitation) and
     with the audio left out while the final state is requested;
-  * at the size limit, where the state region ends next to the end of the
-    1 MiB block, and one mode beyond it, which must be refused.
+  * at the size limit, where the state region ends a few hundred bytes
+    before the end of the 1 MiB block, and one mode beyond it, which must be
+    refused.
 The file sits on its own and is collected last."""
 import ctypes
 
@@ -39,7 +40,7 @@ def _align16(x):
 
 def max_modes(n_inst):
     """The documented limit of include/mdx.h."""
-    return (BLOCK - _align16(120 * n_inst) - _align16(4 * n_inst) - 176) // 44
+    return (BLOCK - _align16(120 * n_inst) - _align16(4 * n_inst) - 192) // 48
 
 
 def _instances(steps):
@@ -183,9 +184,11 @@ def test_noalloc_optional_inputs_and_outputs():
 
 
 def test_noalloc_at_the_size_limit():
-    """24 instances whose modes fill the block up to the documented limit:
-    the state region then ends within 92 bytes of the end of the block."""
-    n_inst, steps = 24, 200
+    """Instances whose modes fill the block up to the documented limit (all
+    but the last with 1024 modes): the state region then ends 208 bytes
+    before the end of the block, and one mode more no longer fits."""
+    steps = 200
+    n_inst = next(n for n in range(1, 64) if max_modes(n) <= 1024 * n)
     total = max_modes(n_inst)
     sizes = [1024] * (n_inst - 1)
     sizes.append(total - sum(sizes))
