@@ -67,6 +67,15 @@ def workload_name(a):
     return (f"adjoint{a.n_inst}_plate{a.n_phi}x{a.n_psi}_{a.sim_steps}steps_K{a.K}")
 
 
+def load_tensor_peak():
+    """Measured dense BF16 tensor throughput (FLOP/s, burst) or the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"]) * 1e12
+    return 1.9e15
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -287,6 +296,10 @@ def forward_workload(a):
             bank.update(b)
         cp = proposal._bank_coupling(bank)
         prep = [physics.prepare(i, wl.fs, wl.steps, coupling=cp) for i in wl.instances]
+        # plates of one aspect share their coupling tensor: one tensor-core group each
+        for inst, p in zip(wl.instances, prep):
+            if inst.kind == "plate":
+                p["geom_group"] = 1 + aspects.index(float(inst.aspect))
     else:
         wl = W.string_40() if a.workload == "string40" else W.plate_100x30()
         prep = [physics.prepare(i, wl.fs, wl.steps) for i in wl.instances]
@@ -311,6 +324,8 @@ def forward_workload(a):
     ms = ev0.elapsed_time(ev1) / a.steps
     value = modes * steps / (ms * 1e-3)
     n, pms, pby = sim.plan.kernel_stats(0)
+    gn, gms, gby = sim.plan.kernel_stats(5)
+    sim.plan.set_profiling(False)
     peak, peak_kind = load_peaks()
     line = {"metric": "mode-steps/s forward", "value": value, "unit": UNIT, "n_gpus": 1,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
@@ -323,7 +338,39 @@ def forward_workload(a):
         line["plate_kernel"] = {"GB/s": ach, "frac_of_hbm": ach / peak,
                                 "peak_source": f"{peak_kind} hbm_gbs",
                                 "share_of_time": pms / (ms * a.steps)}
+    if gn:
+        # grouped plates: one pass over each group's shared coupling tensor per
+        # step; the contraction's algorithmic flops are 2 x (nonzero H entries)
+        # x plates, executed three times over as split TF32
+        ach = gby / (gms * 1e-3) / 1e9
+        tf32_peak = load_tensor_peak() / 2.0
+        fl = sim.plan.group_work()[1] * steps * gn
+        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "traffic": None,
+                "kernel": "group_kernel (split-TF32 tcgen05 GEMM per stress mode and step)",
+                "peak_source": f"{peak_kind} hbm_gbs",
+                "share_of_time": gms / (ms * a.steps),
+                "us_per_step": gms * 1e3 / (gn * steps),
+                "tensor": {"algorithmic_TFLOP/s": fl / (gms * 1e-3) / 1e12,
+                           "executed_TFLOP/s": 3 * fl / (gms * 1e-3) / 1e12,
+                           "tf32_peak_TFLOP/s": tf32_peak / 1e12,
+                           "peak_source": "measured bf16_tflops / 2 (TF32 runs at half the BF16 rate)"}}
+        line["roofline"] = roof
     if a.workload == "batched":
+        # the same plans with every plate on its own coupling copy: the FP32
+        # CUDA-core path of the per-instance kernel
+        csim = modal.Simulator(prep, group_engine="off")
+        csim.simulate(steps)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        csim.simulate(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        cc_ms = ev0.elapsed_time(ev1)
+        line["fp32_cuda_core_per_instance"] = {
+            "value": modes * steps / (cc_ms * 1e-3), "ms_per_step": cc_ms,
+            "grouped_tf32x3_over_fp32": cc_ms / ms}
+        del csim
         # the plain form: one instance per plan and launch, on a seeded subset
         rng = np.random.default_rng(1)
         sub = sorted(rng.choice(len(prep), size=32, replace=False).tolist())

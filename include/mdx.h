@@ -328,6 +328,13 @@ double mdx_plan_l2_keep(const mdx_plan *plan);
  * mdx_plan_reset_stats clears the counters.  Off by default.
  */
 int mdx_plan_set_profiling(mdx_plan *plan, int enable);
+/* Work of the grouped-plate launch per simulated step (bookkeeping for
+ * rooflines; the paper has no counterpart): bytes of the shared coupling
+ * tensors' nonzero class blocks (one pass per step) and the contraction's
+ * algorithmic flops, 2 x (nonzero entries) x (plates of the group), summed
+ * over groups (the split-TF32 form executes three MMAs per product).  Zero for
+ * a plan without grouped plates.  Errors: MDX_ERR_ARG for a NULL plan. */
+int mdx_plan_group_work(const mdx_plan *plan, double *bytes_per_step, double *flops_per_step);
 int mdx_plan_kernel_stats(mdx_plan *plan, int which, long *launches, double *ms, double *bytes);
 int mdx_plan_reset_stats(mdx_plan *plan);
 

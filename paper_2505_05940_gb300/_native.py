@@ -30,7 +30,7 @@ EXPORTED = ("mdx_last_error", "mdx_version", "mdx_plan_create", "mdx_plan_destro
             "mdx_mlp_act_elems", "mdx_mlp_work_elems", "mdx_mlp_forward", "mdx_mlp_backward",
             "mdx_adam_step", "mdx_f32_to_bf16", "mdx_plan_set_l2_keep", "mdx_plan_l2_keep",
             "mdx_difference_coefficients", "mdx_coefficient_grads", "mdx_modal_from_physics",
-            "mdx_physics_vjp")
+            "mdx_physics_vjp", "mdx_plan_group_work")
 
 
 class MdxError(RuntimeError):
@@ -160,6 +160,8 @@ def load(build_if_missing: bool = True):
         L.mdx_plan_l2_keep.restype = ctypes.c_double
         L.mdx_plan_tiles.argtypes = [vp] + [ctypes.POINTER(i32)] * 4
         L.mdx_plan_set_profiling.argtypes = [vp, i32]
+        L.mdx_plan_group_work.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double)]
         L.mdx_plan_reset_stats.argtypes = [vp]
         L.mdx_plan_kernel_stats.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_long),
                                             ctypes.POINTER(ctypes.c_double),
@@ -313,6 +315,12 @@ class Plan:
                     ctas=v[3].value)
 
     # ------------------------------------------------------------------ tracing
+    def group_work(self):
+        """(bytes, flops) per step of the grouped-plate launch (0, 0 if none)."""
+        b, f = ctypes.c_double(), ctypes.c_double()
+        check(load().mdx_plan_group_work(self._h, ctypes.byref(b), ctypes.byref(f)))
+        return b.value, f.value
+
     def set_profiling(self, enable=True):
         check(load().mdx_plan_set_profiling(self._h, 1 if enable else 0))
 

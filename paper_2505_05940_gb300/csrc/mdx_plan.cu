@@ -1399,6 +1399,14 @@ extern "C" int mdx_coeffs_vjp(int n, const double *lambda, double D, double T0, 
     return MDX_OK;
 }
 
+extern "C" int mdx_plan_group_work(const mdx_plan *p, double *bytes_per_step,
+                                   double *flops_per_step) {
+    if (!p) return fail(MDX_ERR_ARG, "plan is NULL");
+    if (bytes_per_step) *bytes_per_step = group_plan_bytes_per_step(p->grp);
+    if (flops_per_step) *flops_per_step = group_plan_flops_per_step(p->grp);
+    return MDX_OK;
+}
+
 extern "C" int mdx_plan_set_profiling(mdx_plan *p, int enable) {
     if (!p) return fail(MDX_ERR_ARG, "plan is NULL");
     p->profiling = enable != 0;
