@@ -23,6 +23,11 @@ Secondary workloads (forward only, one JSON line each, not the headline):
                           with one instance per launch on a seeded subset
   --workload string40     one 40-mode nonlinear string, 48 000 steps at 48 kHz
   --workload plate100x30  one 100 x 30 steel plate, 44 100 steps
+
+C-ABI driver (no PyTorch in the process, for profilers): the benchmark batch
+through mdx_plan_create / mdx_simulate / mdx_grad with device buffers from the
+CUDA runtime and inputs staged from host memory:
+  python bench.py --c-abi --sim-steps 200 --K 64 [--no-grad] [--reps R]
 """
 from __future__ import annotations
 
@@ -60,6 +65,13 @@ def parse():
     ap.add_argument("--workers", type=int, default=0)
     ap.add_argument("--workload", default="adjoint",
                     choices=["adjoint", "batched", "string40", "plate100x30"])
+    ap.add_argument("--fwd-steps", type=int, default=0,
+                    help="forward workloads: simulated steps (0 = the workload's own)")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="batched workload: skip the per-instance and one-per-launch timings")
+    ap.add_argument("--c-abi", action="store_true")
+    ap.add_argument("--no-grad", action="store_true")
+    ap.add_argument("--reps", type=int, default=1)
     return ap.parse_args()
 
 
@@ -214,8 +226,10 @@ class ClockSampler:
 # ----------------------------------------------------------------- CPU oracle
 
 def oracle_sample(a, n_threads, sample_steps):
-    """FP64 oracle forward + adjoint (with dL/dH) of one plate per thread on a
-    bounded number of steps; returns (mode-steps/s, threads, description)."""
+    """FP64 oracle forward + adjoint of one plate per thread on a bounded
+    number of steps (the same outputs mdx_grad gives per mode and stress
+    mode; the oracle has no counterpart of the aspect-direction contraction);
+    returns (mode-steps/s, threads, description)."""
     import oracle
     from oracle import coupling_oracle as CO
     from oracle import physics_oracle as PO
@@ -231,7 +245,7 @@ def oracle_sample(a, n_threads, sample_steps):
     oracle.lib()
 
     def work(oi):
-        oracle.adjoint(oi, ybar, want_dH=True)   # runs the forward (trajectory) then the reverse
+        oracle.adjoint(oi, ybar)   # runs the forward (trajectory) then the reverse
 
     ths = [threading.Thread(target=work, args=(o,)) for o in ois]
     t0 = time.perf_counter()
@@ -242,7 +256,9 @@ def oracle_sample(a, n_threads, sample_steps):
     dt = time.perf_counter() - t0
     value = n_threads * ois[0].N * sample_steps / dt
     desc = (f"{n_threads} thread(s) x one {ois[0].N}x{ois[0].M} plate x {sample_steps} steps "
-            f"forward+adjoint in FP64 (the oracle as it stands), {dt:.1f} s wall")
+            f"forward+adjoint in FP64 (the oracle as it stands), {dt:.1f} s wall; the "
+            f"value is that sample's mode-steps/s, extrapolated to the full workload "
+            f"({a.n_inst} plates x {a.sim_steps} steps) for ms_per_step")
     return value, n_threads, desc
 
 
@@ -306,7 +322,9 @@ def forward_workload(a):
     import torch
     from paper_2505_05940_gb300 import modal
     sim = modal.Simulator(prep)
-    steps = wl.steps
+    steps = a.fwd_steps if a.fwd_steps > 0 else wl.steps
+    if steps > wl.steps:
+        raise SystemExit("--fwd-steps exceeds the workload's excitation length")
     modes = int(sum(len(p["omega2"]) for p in prep))
     for _ in range(a.warmup):
         sim.simulate(steps)
@@ -356,7 +374,7 @@ def forward_workload(a):
                            "tf32_peak_TFLOP/s": tf32_peak / 1e12,
                            "peak_source": "measured bf16_tflops / 2 (TF32 runs at half the BF16 rate)"}}
         line["roofline"] = roof
-    if a.workload == "batched":
+    if a.workload == "batched" and not a.no_compare:
         # the same plans with every plate on its own coupling copy: the FP32
         # CUDA-core path of the per-instance kernel
         csim = modal.Simulator(prep, group_engine="off")
@@ -375,7 +393,7 @@ def forward_workload(a):
         rng = np.random.default_rng(1)
         sub = sorted(rng.choice(len(prep), size=32, replace=False).tolist())
         sub_steps = 2205
-        sims = [modal.Simulator([prep[i]]) for i in sub]
+        sims = [modal.Simulator([prep[i]], group_engine="off") for i in sub]
         for s_ in sims:
             s_.simulate(sub_steps)
         torch.cuda.synchronize()
@@ -402,12 +420,124 @@ def forward_workload(a):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------- C ABI alone
+
+class _Cuda:
+    """Device buffers straight from the CUDA runtime (no PyTorch)."""
+
+    def __init__(self):
+        import ctypes
+        import glob
+        cands = [os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "lib64",
+                              "libcudart.so")]
+        cands += sorted(glob.glob("/usr/local/cuda*/lib64/libcudart.so*"))
+        path = next((c for c in cands if os.path.exists(c)), None)
+        if path is None:
+            raise OSError("libcudart.so not found")
+        self.ct = ctypes
+        self.rt = ctypes.CDLL(path)
+        self.ptrs = []
+
+    def check(self, rc, what):
+        if rc != 0:
+            raise RuntimeError(f"{what}: CUDA error {rc}")
+
+    def alloc(self, nbytes):
+        p = self.ct.c_void_p()
+        self.check(self.rt.cudaMalloc(self.ct.byref(p), self.ct.c_size_t(max(16, nbytes))),
+                   "cudaMalloc")
+        self.ptrs.append(p)
+        return p
+
+    def h2d(self, dst, arr):
+        a = np.ascontiguousarray(arr)
+        self.check(self.rt.cudaMemcpy(dst, a.ctypes.data_as(self.ct.c_void_p),
+                                      self.ct.c_size_t(a.nbytes), 1), "cudaMemcpy")
+
+    def d2h(self, arr, src):
+        self.check(self.rt.cudaMemcpy(arr.ctypes.data_as(self.ct.c_void_p), src,
+                                      self.ct.c_size_t(arr.nbytes), 2), "cudaMemcpy")
+
+    def sync(self):
+        self.check(self.rt.cudaDeviceSynchronize(), "cudaDeviceSynchronize")
+
+    def free(self):
+        for p in self.ptrs:
+            self.rt.cudaFree(p)
+        self.ptrs = []
+
+
+def c_abi_run(a):
+    """The benchmark batch through the C ABI alone: every call's inputs are
+    copied up from host memory and its outputs (audio, per-mode gradients)
+    copied back, inside the timed loop; no PyTorch is loaded."""
+    import ctypes
+    from paper_2505_05940_gb300 import _native
+    _, init_p, _ = prepare_inputs(a, 0)
+    L = _native.load()
+    cu = _Cuda()
+    plan = _native.Plan(init_p)
+    n, steps, K, TM = len(init_p), a.sim_steps, a.K, plan.total_modes
+    grad = not a.no_grad
+    exc = np.zeros((n, steps), np.float32)
+    for i, p in enumerate(init_p):
+        exc[i] = p["e"][:steps]
+    q0 = np.concatenate([p["q0"] for p in init_p]).astype(np.float64)
+    ybar = np.random.default_rng(0).standard_normal((n, steps)).astype(np.float32) * 1e-3
+    d_exc, d_q0, d_qm1 = cu.alloc(exc.nbytes), cu.alloc(q0.nbytes), cu.alloc(q0.nbytes)
+    d_ybar = cu.alloc(ybar.nbytes)
+    audio = cu.alloc(n * steps * 4)
+    ckpt = cu.alloc(plan.checkpoint_bytes(steps, K))
+    status = cu.alloc(n * 4)
+    work_bytes = plan.workspace_bytes(steps, K)
+    work = cu.alloc(work_bytes) if grad else None
+    g = _native.Grads()
+    outs = {}
+    for name, count in (("d_omega2", TM), ("d_gamma", TM), ("d_kappa",
+                        max(1, int(plan.n_stress.sum()))), ("d_dir", n)):
+        outs[name] = (cu.alloc(count * 8), np.zeros(count))
+        setattr(g, name, outs[name][0].value)
+    host_audio = np.zeros((n, steps), np.float32)
+    times = []
+    for _ in range(max(1, a.reps)):
+        cu.sync()
+        t0 = time.perf_counter()
+        cu.h2d(d_exc, exc)
+        cu.h2d(d_q0, q0)
+        cu.h2d(d_qm1, q0)
+        _native.check(L.mdx_simulate(plan._h, d_exc, d_q0, d_qm1, steps, audio, None, None, K,
+                                     ckpt, status, None))
+        cu.d2h(host_audio, audio)
+        if grad:
+            cu.h2d(d_ybar, ybar)
+            _native.check(L.mdx_grad(plan._h, d_exc, d_q0, d_qm1, steps, d_ybar, K, ckpt, work,
+                                     work_bytes, ctypes.byref(g), status, None))
+            for name, (dev, host) in outs.items():
+                cu.d2h(host, dev)
+        cu.sync()
+        times.append(time.perf_counter() - t0)
+    st = np.zeros(n, np.int32)
+    cu.d2h(st, status)
+    ms = min(times) * 1e3
+    print(json.dumps({"c_abi": True, "plates": n, "modes": TM, "steps": steps, "K": K,
+                      "grad": grad, "ms_per_call": ms,
+                      "mode_steps_per_s": n * a.n_phi * steps / (ms * 1e-3),
+                      "status_max": int(st.max())}), flush=True)
+    plan.close()
+    cu.free()
+    if st.max() != 0:
+        raise SystemExit(1)
+
+
 # ----------------------------------------------------------------- main arm
 
 def main():
     a = parse()
     if a.impl == "reference":
         reference_arm(a)
+        return
+    if a.c_abi:
+        c_abi_run(a)
         return
     if a.workload != "adjoint":
         forward_workload(a)
@@ -530,7 +660,10 @@ def main():
                 "config": {"workload": workload_name(a), "instances_per_gpu": a.n_inst,
                            "n_phi": a.n_phi, "n_psi": a.n_psi, "sim_steps": a.sim_steps,
                            "K": a.K, "loss": "multi-resolution log-STFT L1 (256/1024/4096)",
-                           "l2": "inputs larger than L2 (coupling tensors 512 MB per GPU)",
+                           "l2": ("working set larger than L2, no flush: every step re-reads "
+                                  "the class-layout coupling data (128 MB) and each segment its "
+                                  "aspect derivative (128 MB), beside checkpoints and segment "
+                                  "buffers"),
                            "parallelism": f"instances sharded, {world} GPU(s), no collective"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(round(launches_per_step * a.steps)), "clocks": clk.summary(),

@@ -186,6 +186,20 @@ int mdx_plan_set_coefficients(mdx_plan *plan, const double *omega2, const double
                               const double *kappa);
 
 /*
+ * Replace the coupling tensor H (Eq. 10) of plate `inst` in a plan, and its
+ * direction tensor dH if the plate was planned with one (dH NULL keeps it):
+ * host FP32 [M][N][N], symmetric in the last two indices, read during the call
+ * only.  Used when H itself is fitted (Sec. 4.3.3: the coupling coefficients of
+ * the von Karman plate are optimised from a random initialisation).  A plan in
+ * the symmetry-class layout stores only the class pattern, so the new H must
+ * follow it (entries outside it at most 1e-6 of max |H^k|); plan without
+ * classes (dense layout) to fit an unstructured H.  Synchronises the plan's
+ * device.  Errors: MDX_ERR_ARG (index, symmetry, class pattern),
+ * MDX_ERR_NONFINITE, MDX_ERR_UNSUPPORTED (a grouped plate), MDX_ERR_CUDA.
+ */
+int mdx_plan_set_coupling(mdx_plan *plan, int inst, const float *H, const float *dH);
+
+/*
  * Host FP64 coefficients of the difference form the kernels step (Sec. 3.2):
  *   v^{n+1} = v^n - eps v^n - rho q^n + r F^n,  q^{n+1} = q^n + v^{n+1},
  * i.e. the recursion q^{n+1} = g q^n + p q^{n-1} + r F^n of Eq. 20 (scheme
@@ -256,6 +270,12 @@ typedef struct mdx_grads {
     double *d_tau;      /* [n_inst] dL/d tau' (tension instances; 0 for plates) */
     double *d_kappa;    /* [total stress modes] dL/d kappa, plates in plan order */
     double *d_dir;      /* [n_inst] <dL/dH, dH> for plates planned with dH (else 0) */
+    double *d_H;        /* dL/dH^k_ij (Eq. 10; symmetrised over i, j, as H is symmetric):
+                           for each plate with n_psi > 0 in plan order, [n_psi][N][N] in the
+                           instance's own mode order; with the symmetry-class layout the
+                           entries outside the class pattern (structurally zero in H) are
+                           0, i.e. the gradient within class-structured tensors.  Used to fit
+                           the coupling tensor itself (Sec. 4.3.3). */
 } mdx_grads;
 
 /* Bytes of the caller-owned device workspace mdx_grad needs for (steps, K):

@@ -30,7 +30,7 @@ EXPORTED = ("mdx_last_error", "mdx_version", "mdx_plan_create", "mdx_plan_destro
             "mdx_mlp_act_elems", "mdx_mlp_work_elems", "mdx_mlp_forward", "mdx_mlp_backward",
             "mdx_adam_step", "mdx_f32_to_bf16", "mdx_plan_set_l2_keep", "mdx_plan_l2_keep",
             "mdx_difference_coefficients", "mdx_coefficient_grads", "mdx_modal_from_physics",
-            "mdx_physics_vjp", "mdx_plan_group_work")
+            "mdx_physics_vjp", "mdx_plan_group_work", "mdx_plan_set_coupling")
 
 
 class MdxError(RuntimeError):
@@ -96,7 +96,7 @@ class MLPDesc(ctypes.Structure):
 
 class Grads(ctypes.Structure):
     _fields_ = [(n, ctypes.c_void_p) for n in ("d_omega2", "d_gamma", "d_b", "d_c", "d_q0",
-                                                "d_qm1", "d_tau", "d_kappa", "d_dir")]
+                                                "d_qm1", "d_tau", "d_kappa", "d_dir", "d_H")]
 
 
 _lib = None
@@ -138,6 +138,7 @@ def load(build_if_missing: bool = True):
         L.mdx_coeffs_vjp.argtypes = [i32, _D, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, _D, _D, _D, _D, _D, _D, _D]
         L.mdx_plan_set_coefficients.argtypes = [vp, _D, _D, _D, _D, _D, _D]
+        L.mdx_plan_set_coupling.argtypes = [vp, i32, _F, _F]
         L.mdx_modal_from_physics.argtypes = [ctypes.POINTER(Physics), ctypes.POINTER(Modal)]
         L.mdx_physics_vjp.argtypes = [ctypes.POINTER(Physics), i32, i32, _D, _D,
                                       ctypes.c_double, _D, ctypes.c_double, _D,
@@ -296,6 +297,13 @@ class Plan:
         keep = []
         check(load().mdx_plan_set_coefficients(self._h, dp(omega2), dp(gamma), dp(b), dp(c),
                                                dp(tau), dp(kappa)))
+
+    def set_coupling(self, inst, H, dH=None):
+        """New coupling tensor [M][N][N] (host FP32) for plate `inst`."""
+        h = np.ascontiguousarray(H, dtype=np.float32)
+        d = None if dH is None else np.ascontiguousarray(dH, dtype=np.float32)
+        check(load().mdx_plan_set_coupling(self._h, int(inst), h.ctypes.data_as(_F),
+                                           d.ctypes.data_as(_F) if d is not None else None))
 
     # ------------------------------------------------------------------ tiles
     def configure(self, stage_bytes=0, ring_stages=0):

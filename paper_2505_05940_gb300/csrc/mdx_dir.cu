@@ -14,6 +14,11 @@
 // blocks (all of H^k for the dense layout, the four symmetry-class blocks for
 // the class layout) in 64 x 64 output tiles, 4 x 4 per thread, over step
 // tiles of 32 held in shared memory.
+//
+// The same kernels give the full gradient dL/dH (WRITE = true): instead of
+// the contraction with dH, -kappa_k G_k is added into an FP64 output in each
+// plate's own mode order; after the last segment the output is symmetrised,
+// dL/dH^k_ij = -kappa_k (G_k + G_k^T)_ij / 2, since H^k is symmetric.
 #include <cuda_runtime.h>
 
 #include "mdx_common.cuh"
@@ -32,6 +37,7 @@ __device__ __forceinline__ int pick4d(const int (&v)[4], int a) {
 
 }  // namespace
 
+template <bool WRITE>
 __global__ void __launch_bounds__(kDirThreads) dir_contract_kernel(const DirParams P) {
     __shared__ float Zt[kTile][kStepTile + 1];
     __shared__ float Qt[kTile][kStepTile + 1];
@@ -114,31 +120,53 @@ __global__ void __launch_bounds__(kDirThreads) dir_contract_kernel(const DirPara
                     }
                     __syncthreads();
                 }
-                // <dH block tile, G tile>
+                if constexpr (WRITE) {
+                    // -kappa_k G_k into the plate's [k][i][j] block (user order)
+                    const double sc = -(double)P.kappa[kk];
+                    const int ku = P.kperm[kk];
+                    double *blkout = P.dH_out + P.dh_off[U.inst] + (long long)ku * d.N * d.N;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int rr = r0 + tr * 4 + i;
-                    if (rr >= nr) continue;
+                    for (int i = 0; i < 4; ++i) {
+                        const int rr = r0 + tr * 4 + i;
+                        if (rr >= nr) continue;
+                        const int mi = d.parity ? P.perm[d.perm_off + orow + rr] : orow + rr;
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int cc = c0 + tc * 4 + j;
-                        if (cc >= nc) continue;
-                        const float h = d.parity ? blk[((long long)rr * mc + kl) * nb4 + cc]
-                                                 : blk[(long long)rr * d.Npad + cc];
-                        part = fmaf(h, acc[i][j], part);
+                        for (int j = 0; j < 4; ++j) {
+                            const int cc = c0 + tc * 4 + j;
+                            if (cc >= nc) continue;
+                            const int mj = d.parity ? P.perm[d.perm_off + ocol + cc] : ocol + cc;
+                            blkout[(long long)mi * d.N + mj] += sc * (double)acc[i][j];
+                        }
+                    }
+                } else {
+                    // <dH block tile, G tile>
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int rr = r0 + tr * 4 + i;
+                        if (rr >= nr) continue;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int cc = c0 + tc * 4 + j;
+                            if (cc >= nc) continue;
+                            const float h = d.parity ? blk[((long long)rr * mc + kl) * nb4 + cc]
+                                                     : blk[(long long)rr * d.Npad + cc];
+                            part = fmaf(h, acc[i][j], part);
+                        }
                     }
                 }
             }
         }
     }
-    part = warp_sum(part);
-    if ((tid & 31) == 0) red[tid >> 5] = part;
-    __syncthreads();
-    if (tid == 0) {
-        float t = 0.f;
-        for (int w = 0; w < kDirThreads / 32; ++w) t += red[w];
-        const float kap = P.kappa[kk];
-        P.dir_acc[kk * 4] += -(double)kap * (double)t;
+    if constexpr (!WRITE) {
+        part = warp_sum(part);
+        if ((tid & 31) == 0) red[tid >> 5] = part;
+        __syncthreads();
+        if (tid == 0) {
+            float t = 0.f;
+            for (int w = 0; w < kDirThreads / 32; ++w) t += red[w];
+            const float kap = P.kappa[kk];
+            P.dir_acc[kk * 4] += -(double)kap * (double)t;
+        }
     }
 }
 
@@ -148,6 +176,7 @@ __global__ void __launch_bounds__(kDirThreads) dir_contract_kernel(const DirPara
 // over the segment's steps, with z_k^n = xi_k^n q_a^n + eta_k^n w_a^n formed on
 // the fly from shared-memory state tiles; then <dH^k_ab, G_k> per mode.
 constexpr int kDirKB = 4;
+template <bool WRITE>
 __global__ void __launch_bounds__(kDirThreads) dir_class_kernel(const DirParams P) {
     __shared__ float Qc[kTile][kStepTile + 1];
     __shared__ float Qr[kTile][kStepTile + 1];
@@ -229,6 +258,31 @@ __global__ void __launch_bounds__(kDirThreads) dir_class_kernel(const DirParams 
                         }
                     }
                 }
+                if constexpr (WRITE) {
+                    // -kappa_k G_k into the plate's [k][i][j] block (user order)
+                    for (int q = 0; q < kDirKB; ++q) {
+                        if (q >= nkb) break;
+                        const DirUnit u = P.units[Gp.unit0 + kb + q];
+                        const long long kk = d.k_off + u.kl;
+                        const double sc = -(double)P.kappa[kk];
+                        double *blkout = P.dH_out + P.dh_off[Gp.inst] +
+                                         (long long)P.kperm[kk] * d.N * d.N;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int rr = r0 + tr * 4 + i;
+                            if (rr >= nr) continue;
+                            const int mi = P.perm[d.perm_off + orow + rr];
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                const int cc = c0 + tc * 4 + j;
+                                if (cc >= nc) continue;
+                                const int mj = P.perm[d.perm_off + ocol + cc];
+                                blkout[(long long)mi * d.N + mj] += sc * (double)acc[q][i][j];
+                            }
+                        }
+                    }
+                    continue;
+                }
                 // <dH^k tile, G_k tile>
 #pragma unroll
                 for (int q = 0; q < kDirKB; ++q) {
@@ -254,6 +308,7 @@ __global__ void __launch_bounds__(kDirThreads) dir_class_kernel(const DirParams 
                 }
             }
         }
+        if constexpr (WRITE) continue;
 #pragma unroll
         for (int q = 0; q < kDirKB; ++q) {
             const float v = warp_sum(tot[q]);
@@ -272,11 +327,50 @@ __global__ void __launch_bounds__(kDirThreads) dir_class_kernel(const DirParams 
 
 cudaError_t launch_dir_contract(const DirParams &p, int n_units, cudaStream_t s) {
     if (p.groups && p.n_groups > 0) {
-        dir_class_kernel<<<p.n_groups, kDirThreads, 0, s>>>(p);
+        dir_class_kernel<false><<<p.n_groups, kDirThreads, 0, s>>>(p);
         return cudaGetLastError();
     }
     if (n_units <= 0) return cudaSuccess;
-    dir_contract_kernel<<<n_units, kDirThreads, 0, s>>>(p);
+    dir_contract_kernel<false><<<n_units, kDirThreads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dH_accumulate(const DirParams &p, int n_units, cudaStream_t s) {
+    if (p.groups && p.n_groups > 0) {
+        dir_class_kernel<true><<<p.n_groups, kDirThreads, 0, s>>>(p);
+        return cudaGetLastError();
+    }
+    if (n_units <= 0) return cudaSuccess;
+    dir_contract_kernel<true><<<n_units, kDirThreads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+namespace {
+
+__global__ void dh_symmetrize_kernel(double *dH, const long long *dh_off, const InstDesc *inst,
+                                     const int *plates) {
+    const InstDesc d = inst[plates[blockIdx.y]];
+    double *base = dH + dh_off[plates[blockIdx.y]];
+    const long long N = d.N, total = (long long)d.M * N * N;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long k = e / (N * N), r = e - k * N * N;
+        const long long i = r / N, j = r - i * N;
+        if (i >= j) continue;
+        double *a = base + k * N * N + i * N + j;
+        double *b = base + k * N * N + j * N + i;
+        const double m = 0.5 * (*a + *b);
+        *a = m;
+        *b = m;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_dH_symmetrize(double *dH, const long long *dh_off, const InstDesc *inst,
+                                 const int *plates, int n_plates, cudaStream_t s) {
+    if (n_plates <= 0) return cudaSuccess;
+    dh_symmetrize_kernel<<<dim3(64, n_plates), 256, 0, s>>>(dH, dh_off, inst, plates);
     return cudaGetLastError();
 }
 

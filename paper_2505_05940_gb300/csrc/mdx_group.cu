@@ -240,6 +240,50 @@ __device__ __forceinline__ int cm_index(int row, int col, int kcols) {
     return (((row >> 3) * (kcols >> 2) + (col >> 2)) << 5) + ((row & 7) << 2) + (col & 3);
 }
 
+// Writes q of plate b at class-order position pos into a Q image (global or
+// shared): TF32 high part in class a's image, the FP32 remainder in the image
+// that follows it.
+__device__ __forceinline__ void q_image_put(float *img, const GrpDesc &G, int b, int pos, float q) {
+    int a = 0;
+    if (pos >= G.ocls[1]) a = 1;
+    if (pos >= G.ocls[2]) a = 2;
+    if (pos >= G.ocls[3]) a = 3;
+    const int kp = G.kpad[a];
+    const int e = G.qoff[a] + cm_index(b, pos - G.ocls[a], kp);
+    const float h = tf32_hi(q);
+    img[e] = h;
+    img[e + G.Bp * kp] = q - h;
+}
+
+// Proxy fence: global-memory writes seen through the generic proxy become
+// visible to the bulk copies (async proxy) this thread issues next.
+__device__ __forceinline__ void fence_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// In-warp reduction of 16 values per lane: on return, lane l (l even) holds
+// the warp's sum of value ((l >> 4) & 1) * 8 + ((l >> 3) & 1) * 4 +
+// ((l >> 2) & 1) * 2 + ((l >> 1) & 1), after 16 shuffles instead of 80.
+__device__ __forceinline__ float warp_reduce16(float (&t)[16], int lane) {
+#pragma unroll
+    for (int half = 8, o = 16; half >= 1; half >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (i < half) {
+                const float keep = up ? t[i + half] : t[i];
+                const float send = up ? t[i] : t[i + half];
+                t[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+        }
+    }
+    return t[0] + __shfl_xor_sync(0xffffffffu, t[0], 1);
+}
+
+__device__ __forceinline__ int reduce16_index(int lane) {
+    return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+}
+
 struct Ctrl {
     uint64_t full[8], empty[8], conv[8];
     uint64_t qready, mma_done, epi_free, drain;
@@ -475,8 +519,8 @@ __global__ void __launch_bounds__(kGrpThreads, 1) group_kernel(const GroupParams
             if (pl.owner != cta) continue;
             const InstDesc d = P.inst[pl.inst];
             for (int j = et; j < d.N; j += 128)
-                P.qbuf[G.qbuf_off + (long long)b * G.Np + P.gpos[G.gpos_off + j]] =
-                    P.state_io[d.mode_off + j];
+                q_image_put(P.qbuf + G.qbuf_off, G, b, P.gpos[G.gpos_off + j],
+                            P.state_io[d.mode_off + j]);
         }
         epi_bar();
         if (et == 0) {
@@ -506,25 +550,19 @@ __global__ void __launch_bounds__(kGrpThreads, 1) group_kernel(const GroupParams
                 ok = false;
                 break;
             }
-            for (int a = 0; a < 4; ++a) {
-                const int kp = G.kpad[a];
-                if (kp == 0) continue;
-                float *qh = qimg + G.qoff[a];
-                float *ql = qh + Bp * kp;
-                for (int idx = et; idx < Bp * kp; idx += 128) {
-                    const int b = idx / kp, p = idx - b * kp;
-                    const float v = (b < G.B && p < G.ncls[a])
-                                        ? ldcg(P.qbuf + G.qbuf_off + (long long)b * G.Np + G.ocls[a] + p)
-                                        : 0.f;
-                    const float h = tf32_hi(v);
-                    const int e = cm_index(b, p, kp);
-                    qh[e] = h;
-                    ql[e] = v - h;
-                }
+            // the group's Q image (TF32 high parts and remainders, as the MMAs read
+            // them) comes in with bulk copies; the MMA issuer and this warp group
+            // wait on the same barrier
+            if (et == 0) {
+                fence_async_global();
+                const uint32_t total = (uint32_t)G.q_floats * 4u;
+                bar_expect_tx(&C.qready, total);
+                for (uint32_t o = 0; o < total; o += 32768u)
+                    bulk_load(reinterpret_cast<unsigned char *>(qimg) + o,
+                              reinterpret_cast<const unsigned char *>(P.qbuf + G.qbuf_off) + o,
+                              min(32768u, total - o), &C.qready, false, 0ull);
             }
-            fence_async_smem();
-            epi_bar();
-            if (et == 0) bar_arrive(&C.qready);
+            if (!bar_wait(&C.qready, (uint32_t)(it & 1), P.wait_limit, gabort)) C.fail = 1;
             // ---- zero the force accumulators
             {
                 float z[16];
@@ -568,13 +606,8 @@ __global__ void __launch_bounds__(kGrpThreads, 1) group_kernel(const GroupParams
                             }
                         }
                     }
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        float s = acc[i];
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                        if (lane == 0) C.eta_red[quarter][cb + i] = s;
-                    }
+                    const float sum = warp_reduce16(acc, lane);
+                    if ((lane & 1) == 0) C.eta_red[quarter][cb + reduce16_index(lane)] = sum;
                 }
                 epi_bar();
                 if (et < Bp) {
@@ -652,7 +685,7 @@ __global__ void __launch_bounds__(kGrpThreads, 1) group_kernel(const GroupParams
                         P.state_io[TM + m] = x1;
                         P.state_io[2 * TM + m] = x2;
                         P.state_io[3 * TM + m] = x3;
-                        P.qbuf[G.qbuf_off + (long long)b * G.Np + pos] = x0;
+                        q_image_put(P.qbuf + G.qbuf_off, G, b, pos, x0);
                     }
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
@@ -1006,6 +1039,7 @@ int group_plan_build(GroupPlan **out, const mdx_instance *I, const std::vector<I
             qf += 2 * d.Bp * d.kpad[a];
         }
         q_floats_max = std::max(q_floats_max, qf);
+        d.q_floats = qf;
         d.cta0 = cta;
         d.n_ctas = ctas[g];
         d.plate0 = (int)gp->plates.size();
@@ -1061,7 +1095,7 @@ int group_plan_build(GroupPlan **out, const mdx_instance *I, const std::vector<I
         gp->plate_inst.push_back(pi);
         kap_off += (long long)nu * d.Bp;
         part_off += (long long)d.n_ctas * d.Bp * d.Np;
-        qbuf_off += (long long)d.Bp * d.Np;
+        qbuf_off += (qf + 63) / 64 * 64;   // 256-byte aligned images
         cta += d.n_ctas;
         gp->groups.push_back(d);
     }
@@ -1091,9 +1125,11 @@ int group_plan_build(GroupPlan **out, const mdx_instance *I, const std::vector<I
     if (e == cudaSuccess) e = cudaMalloc(&gp->d_part, std::max<long long>(part_off, 1) * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&gp->d_qbuf, std::max<long long>(qbuf_off, 1) * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&gp->d_counters, std::max(ng, 1) * sizeof(unsigned));
+    // every plan sets the same (largest) limit, so plans of different sizes can
+    // launch in any order
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)gp->smem);
+                                 smem_optin);
     if (e != cudaSuccess) {
         const int code = (e == cudaErrorMemoryAllocation) ? MDX_ERR_OOM : MDX_ERR_CUDA;
         return bail(gfail(code, cudaGetErrorString(e)));

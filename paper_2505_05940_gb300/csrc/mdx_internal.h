@@ -171,6 +171,8 @@ struct PlateParams {
     float *kacc;                  // [total stress modes][2] d kappa (Kahan pair)
     float *seg_w;                 // reverse: [steps][total_modes] w^n = r a^{n+1} (owners)
     float *xe;                    // reverse: [steps][2][total_k] xi_k^n, eta_k^n
+    int xe_all;                   // 1: store xi, eta for every plate (full dL/dH), else
+                                  // only for plates with a direction tensor
     long long total_k;
     // synchronisation
     float *part;                  // exchange slots, two parities of part_stride floats
@@ -213,6 +215,10 @@ struct DirParams {
     double *dir_acc;              // [total_k][4] (class layout: one slot per row class)
     int steps;
     long long total_modes, total_k;
+    // full dL/dH: -kappa_k G_k accumulated into the user-layout output
+    double *dH_out;               // [per plate: M][N][N]
+    const long long *dh_off;      // [n_inst] double offset of each plate's block
+    const int *kperm;             // internal stress index -> user index (at k_off)
 };
 
 struct TensionParams {
@@ -265,7 +271,10 @@ struct GrpDesc {
     long long gpos_off;     // gpos[gpos_off + j] = class position of mode j
     long long kap_off;      // kappa table [units of the group][Bp], 0 where a plate lacks the mode
     long long part_off;     // partial forces [n_ctas][Bp][Np] (class order)
-    long long qbuf_off;     // current q_hi [Bp][Np] (class order), written by the owners
+    long long qbuf_off;     // the group's Q image in global memory (the layout of the
+                            // shared-memory Q region), written by the owners
+    int q_floats;           // floats of the Q region (all classes, high and low parts)
+    int pad2;
 };
 
 // One stress mode of a kernel group (the MMA and epilogue work unit).
@@ -361,5 +370,10 @@ struct GradEpilogue {
 };
 cudaError_t launch_grad_epilogue(const GradEpilogue &g, int max_n, cudaStream_t s);
 cudaError_t launch_dir_contract(const DirParams &p, int n_units, cudaStream_t s);
+// Adds -kappa_k G_k of one segment into p.dH_out (units / groups over every plate).
+cudaError_t launch_dH_accumulate(const DirParams &p, int n_units, cudaStream_t s);
+// dH_out[k][i][j] = dH_out[k][j][i] = their mean, for every plate.
+cudaError_t launch_dH_symmetrize(double *dH, const long long *dh_off, const InstDesc *inst,
+                                 const int *plates, int n_plates, cudaStream_t s);
 
 }  // namespace mdx

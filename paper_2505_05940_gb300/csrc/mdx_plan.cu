@@ -120,6 +120,19 @@ struct mdx_plan {
     int n_dir_units = 0;
     DirGroup *d_dir_groups = nullptr;
     int n_dir_groups = 0;
+    // the same units over every plate, for the full dL/dH output
+    DirUnit *d_all_units = nullptr;
+    int n_all_units = 0;
+    DirGroup *d_all_groups = nullptr;
+    int n_all_groups = 0;
+    long long *d_dh_off = nullptr;   // [n_inst] offset (doubles) of each plate's dL/dH block
+    int *d_dh_plates = nullptr;      // plates with stress modes (per-instance path)
+    int n_dh_plates = 0;
+    long long dh_total = 0;          // doubles of the dL/dH output
+    // host copies of the layout, for mdx_plan_set_coupling
+    std::vector<PlateItem> h_items;
+    std::vector<ParityChunk> h_chunks;
+    std::vector<std::vector<int>> h_perm;
     // host copies for coefficient updates
     std::vector<double> h_omega2, h_gamma, h_b, h_c, h_tau, h_kappa;
     std::vector<int> h_kperm;      // internal stress index -> user index, at each k_off
@@ -228,6 +241,61 @@ struct Piece {
 
 int configure_tiles(mdx_plan *p, int stage_req, int ring_req);
 void update_l2_keep(mdx_plan *p);
+
+// Packs the coupling tensor H (and the direction tensor dH, if the plate has
+// one and dH is not NULL) of plate i into the plan's device layout: dense rows
+// [M][N][N_pad], or the symmetry-class chunks of the plate's work items.
+int upload_coupling(mdx_plan *p, int i, const float *H, const float *dH) {
+    const InstDesc &d = p->inst[i];
+    auto nb4 = [](int n) { return (n + 3) & ~3; };
+    std::vector<float> tmp;
+    if (p->parity) {
+        const std::vector<int> &perm = p->h_perm[i];
+        for (const auto &it : p->h_items) {
+            if (it.inst != i) continue;
+            for (int ci = it.chunk0; ci < it.chunk1; ++ci) {
+                const ParityChunk &ch = p->h_chunks[ci];
+                for (int which = 0; which < (d.has_dir ? 2 : 1); ++which) {
+                    const float *src = which == 0 ? H : dH;
+                    if (!src) continue;
+                    tmp.clear();
+                    for (int a = 0; a < 4; ++a) {
+                        const int bcl = a ^ ch.c, na = d.ncls[a], nbc = d.ncls[bcl];
+                        const int w = nb4(nbc);
+                        for (int pp = 0; pp < na; ++pp) {
+                            const int row = perm[d.ocls[a] + pp];
+                            for (int kl = 0; kl < ch.mc; ++kl) {
+                                const int ku = p->h_kperm[d.k_off + ch.kl0 + kl];
+                                const float *Hr = src + ((size_t)ku * d.N + row) * d.N;
+                                for (int cs = 0; cs < w; ++cs)
+                                    tmp.push_back(cs < nbc ? Hr[perm[d.ocls[bcl] + cs]] : 0.f);
+                            }
+                        }
+                    }
+                    float *dst = p->d_H + (which == 0 ? ch.off : ch.doff);
+                    if (!tmp.empty())
+                        MDX_CUDA(cudaMemcpy(dst, tmp.data(), tmp.size() * sizeof(float),
+                                            cudaMemcpyHostToDevice), "upload H");
+                }
+            }
+        }
+    } else {
+        const size_t blk = (size_t)d.M * d.N * d.Npad;
+        for (int which = 0; which < (d.has_dir ? 2 : 1); ++which) {
+            const float *src = which == 0 ? H : dH;
+            if (!src) continue;
+            tmp.assign(blk, 0.f);
+            for (int k = 0; k < d.M; ++k)
+                for (int a2 = 0; a2 < d.N; ++a2)
+                    std::memcpy(&tmp[((size_t)k * d.N + a2) * d.Npad], src + ((size_t)k * d.N + a2) * d.N,
+                                d.N * sizeof(float));
+            float *dst = p->d_H + (which == 0 ? d.H_off : d.dH_off);
+            MDX_CUDA(cudaMemcpy(dst, tmp.data(), blk * sizeof(float), cudaMemcpyHostToDevice),
+                     "upload H");
+        }
+    }
+    return MDX_OK;
+}
 
 }  // namespace
 
@@ -723,52 +791,13 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
             int rc2 = dalloc(p, reinterpret_cast<void **>(&p->d_H), std::max<long long>(H_total, 4) * sizeof(float));
             if (rc2) return bail(rc2);
             p->d_dH = p->d_H;
-            std::vector<float> tmp;
-            if (parity) {
-                for (const auto &it : items) {
-                    const InstDesc &d = p->inst[it.inst];
-                    for (int ci = it.chunk0; ci < it.chunk1; ++ci) {
-                        const ParityChunk &ch = chunks[ci];
-                        for (int which = 0; which < (d.has_dir ? 2 : 1); ++which) {
-                            const float *src = which == 0 ? I[it.inst].H : I[it.inst].dH;
-                            tmp.clear();
-                            for (int a = 0; a < 4; ++a) {
-                                const int bcl = a ^ ch.c, na = d.ncls[a], nbc = d.ncls[bcl];
-                                const int w = nb4(nbc);
-                                for (int pp = 0; pp < na; ++pp) {
-                                    const int row = perm[it.inst][d.ocls[a] + pp];
-                                    for (int kl = 0; kl < ch.mc; ++kl) {
-                                        const int ku = kperm[it.inst][ch.kl0 + kl];
-                                        const float *Hr = src + ((size_t)ku * d.N + row) * d.N;
-                                        for (int cs = 0; cs < w; ++cs)
-                                            tmp.push_back(cs < nbc ? Hr[perm[it.inst][d.ocls[bcl] + cs]] : 0.f);
-                                    }
-                                }
-                            }
-                            float *dst = p->d_H + (which == 0 ? ch.off : ch.doff);
-                            if (!tmp.empty())
-                                MDX_CUDA(cudaMemcpy(dst, tmp.data(), tmp.size() * sizeof(float),
-                                                    cudaMemcpyHostToDevice), "upload H");
-                        }
-                    }
-                }
-            } else {
-                for (int i = 0; i < n_inst; ++i) {
-                    const InstDesc &d = p->inst[i];
-                    if (d.M == 0) continue;
-                    const size_t blk = (size_t)d.M * d.N * d.Npad;
-                    for (int which = 0; which < (d.has_dir ? 2 : 1); ++which) {
-                        const float *src = which == 0 ? I[i].H : I[i].dH;
-                        tmp.assign(blk, 0.f);
-                        for (int k = 0; k < d.M; ++k)
-                            for (int a2 = 0; a2 < d.N; ++a2)
-                                std::memcpy(&tmp[((size_t)k * d.N + a2) * d.Npad],
-                                            src + ((size_t)k * d.N + a2) * d.N, d.N * sizeof(float));
-                        float *dst = p->d_H + (which == 0 ? d.H_off : d.dH_off);
-                        MDX_CUDA(cudaMemcpy(dst, tmp.data(), blk * sizeof(float), cudaMemcpyHostToDevice),
-                                 "upload H");
-                    }
-                }
+            p->h_items = items;
+            p->h_chunks = chunks;
+            p->h_perm = perm;
+            for (int i = 0; i < n_inst; ++i) {
+                if (p->inst[i].M == 0) continue;
+                const int rcu = upload_coupling(p, i, I[i].H, I[i].dH);
+                if (rcu) return bail(rcu);
             }
             // algorithmic bytes of one pass (the stored, structurally nonzero part of H)
             for (int i = 0; i < n_inst; ++i) {
@@ -805,64 +834,88 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
             if ((rc2 = upload(p, &p->d_perm, perm_all.data(), perm_all.size()))) return bail(rc2);
             if ((rc2 = upload(p, &p->d_kperm, kperm_all.data(), kperm_all.size()))) return bail(rc2);
             if ((rc2 = upload(p, &p->d_chunks, chunks.data(), chunks.size()))) return bail(rc2);
-            std::vector<DirUnit> units;
-            if (parity) {
-                for (const auto &it : items) {
-                    if (!p->inst[it.inst].has_dir) continue;
-                    for (int ci = it.chunk0; ci < it.chunk1; ++ci)
-                        for (int q = 0; q < chunks[ci].mc; ++q) {
+            // contraction units: plates with a direction tensor (direction
+            // derivative), and every plate (full dL/dH output)
+            auto build_units = [&](bool all, std::vector<DirUnit> &units,
+                                   std::vector<DirGroup> &groups) {
+                if (parity) {
+                    for (const auto &it : items) {
+                        if (!all && !p->inst[it.inst].has_dir) continue;
+                        for (int ci = it.chunk0; ci < it.chunk1; ++ci)
+                            for (int q = 0; q < chunks[ci].mc; ++q) {
+                                DirUnit u{};
+                                u.inst = it.inst;
+                                u.kl = chunks[ci].kl0 + q;
+                                u.c = chunks[ci].c;
+                                u.mc = chunks[ci].mc;
+                                u.kpos = q;
+                                u.off = chunks[ci].doff;
+                                units.push_back(u);
+                            }
+                    }
+                } else {
+                    for (int i = 0; i < n_inst; ++i) {
+                        const InstDesc &d = p->inst[i];
+                        if (d.M == 0 || (!all && !d.has_dir)) continue;
+                        for (int k = 0; k < d.M; ++k) {
                             DirUnit u{};
-                            u.inst = it.inst;
-                            u.kl = chunks[ci].kl0 + q;
-                            u.c = chunks[ci].c;
-                            u.mc = chunks[ci].mc;
-                            u.kpos = q;
-                            u.off = chunks[ci].doff;
+                            u.inst = i;
+                            u.kl = k;
+                            u.mc = 1;
                             units.push_back(u);
                         }
-                }
-            } else {
-                for (int i = 0; i < n_inst; ++i) {
-                    const InstDesc &d = p->inst[i];
-                    if (!d.has_dir) continue;
-                    for (int k = 0; k < d.M; ++k) {
-                        DirUnit u{};
-                        u.inst = i;
-                        u.kl = k;
-                        u.mc = 1;
-                        units.push_back(u);
                     }
                 }
-            }
-            std::stable_sort(units.begin(), units.end(), [](const DirUnit &x, const DirUnit &y) {
-                return x.inst != y.inst ? x.inst < y.inst : x.kl < y.kl;
-            });
-            std::vector<DirGroup> groups;
-            if (parity) {
-                // class-c stress modes of a plate are contiguous in internal order
-                size_t u0 = 0;
-                while (u0 < units.size()) {
-                    size_t u1 = u0;
-                    while (u1 < units.size() && units[u1].inst == units[u0].inst &&
-                           units[u1].c == units[u0].c)
-                        ++u1;
-                    for (int a = 0; a < 4; ++a) {
-                        DirGroup gr{};
-                        gr.inst = units[u0].inst;
-                        gr.c = units[u0].c;
-                        gr.a = a;
-                        gr.unit0 = (int)u0;
-                        gr.nk = (int)(u1 - u0);
-                        const InstDesc &d = p->inst[gr.inst];
-                        if (d.ncls[a] > 0 && d.ncls[a ^ gr.c] > 0) groups.push_back(gr);
+                std::stable_sort(units.begin(), units.end(), [](const DirUnit &x, const DirUnit &y) {
+                    return x.inst != y.inst ? x.inst < y.inst : x.kl < y.kl;
+                });
+                if (parity) {
+                    // class-c stress modes of a plate are contiguous in internal order
+                    size_t u0 = 0;
+                    while (u0 < units.size()) {
+                        size_t u1 = u0;
+                        while (u1 < units.size() && units[u1].inst == units[u0].inst &&
+                               units[u1].c == units[u0].c)
+                            ++u1;
+                        for (int a = 0; a < 4; ++a) {
+                            DirGroup gr{};
+                            gr.inst = units[u0].inst;
+                            gr.c = units[u0].c;
+                            gr.a = a;
+                            gr.unit0 = (int)u0;
+                            gr.nk = (int)(u1 - u0);
+                            const InstDesc &d = p->inst[gr.inst];
+                            if (d.ncls[a] > 0 && d.ncls[a ^ gr.c] > 0) groups.push_back(gr);
+                        }
+                        u0 = u1;
                     }
-                    u0 = u1;
                 }
-            }
+            };
+            std::vector<DirUnit> units, all_units;
+            std::vector<DirGroup> groups, all_groups;
+            build_units(false, units, groups);
+            build_units(true, all_units, all_groups);
             p->n_dir_units = (int)units.size();
             p->n_dir_groups = (int)groups.size();
             if ((rc2 = upload(p, &p->d_dir_units, units.data(), units.size()))) return bail(rc2);
             if ((rc2 = upload(p, &p->d_dir_groups, groups.data(), groups.size()))) return bail(rc2);
+            p->n_all_units = (int)all_units.size();
+            p->n_all_groups = (int)all_groups.size();
+            if ((rc2 = upload(p, &p->d_all_units, all_units.data(), all_units.size()))) return bail(rc2);
+            if ((rc2 = upload(p, &p->d_all_groups, all_groups.data(), all_groups.size()))) return bail(rc2);
+            std::vector<long long> dh_off(n_inst, 0);
+            std::vector<int> dh_plates;
+            for (int i = 0; i < n_inst; ++i) {
+                const InstDesc &d = p->inst[i];
+                dh_off[i] = p->dh_total;
+                if (d.M > 0) {
+                    p->dh_total += (long long)d.M * d.N * d.N;
+                    dh_plates.push_back(i);
+                }
+            }
+            p->n_dh_plates = (int)dh_plates.size();
+            if ((rc2 = upload(p, &p->d_dh_off, dh_off.data(), dh_off.size()))) return bail(rc2);
+            if ((rc2 = upload(p, &p->d_dh_plates, dh_plates.data(), dh_plates.size()))) return bail(rc2);
         }
         p->min_stage_floats = p->npad_max;
         if (parity) {
@@ -959,8 +1012,9 @@ int configure_tiles(mdx_plan *p, int stage_req, int ring_req) {
         rings[which] = ring;
         smems[which] = need;
     }
-    MDX_CUDA(plate_set_smem_limit(std::max(smems[0], std::max(smems[1], smems[2]))),
-             "cudaFuncSetAttribute");
+    // the device's limit, the same for every plan, so that plans of different
+    // tile shapes can launch in any order
+    MDX_CUDA(plate_set_smem_limit((size_t)smem_optin), "cudaFuncSetAttribute");
     p->stage_bytes = stage;
     p->u_slots_fwd = us_fwd;
     p->u_slots_rev = us_rev;
@@ -1152,7 +1206,8 @@ GradWork grad_layout(const mdx_plan *p, int K, void *base) {
     w.gacc = take(2 * GA_N * TM);
     w.kacc = take(2 * TK);
     w.tacc = take(2 * (size_t)p->n_inst);
-    const bool dir = p->n_dir_units > 0;
+    // w^n and (xi, eta) per step: for the direction contraction and the full dL/dH
+    const bool dir = p->n_all_units > 0;
     w.seg_w = dir ? take((size_t)K * TM) : nullptr;
     w.xe = dir ? take((size_t)K * 2 * TK) : nullptr;
     w.dir_acc = reinterpret_cast<double *>(take(8 * TK));
@@ -1193,6 +1248,8 @@ extern "C" int mdx_grad(mdx_plan *p, const float *exc, const double *q0, const d
     MDX_CUDA(cudaMemsetAsync(w.kacc, 0, 2 * TK * sizeof(float), s), "memset");
     MDX_CUDA(cudaMemsetAsync(w.dir_acc, 0, 4 * TK * sizeof(double), s), "memset");
     MDX_CUDA(cudaMemsetAsync(w.tacc, 0, 2 * p->n_inst * sizeof(float), s), "memset");
+    double *dH_out = (out && out->d_H && p->dh_total > 0) ? out->d_H : nullptr;
+    if (dH_out) MDX_CUDA(cudaMemsetAsync(dH_out, 0, p->dh_total * sizeof(double), s), "memset dH");
     MDX_CUDA(launch_init_adjoint(p->d_inst, p->n_inst, p->coef.c, d_audio, steps, w.adj,
                                  p->total_modes, 0, s),
              "init adjoint");
@@ -1229,11 +1286,32 @@ extern "C" int mdx_grad(mdx_plan *p, const float *exc, const double *q0, const d
         P.kacc = w.kacc;
         P.seg_w = w.seg_w;
         P.xe = w.xe;
+        P.xe_all = dH_out ? 1 : 0;
         P.total_k = p->total_k;
         T.tacc = w.tacc;
     };
-    // direction contraction of segment sg (reads its stored states)
+    // direction contraction of segment sg (reads its stored states), and its
+    // share of the full dL/dH
     auto direction = [&](int sg, const float *sq) -> int {
+        if (dH_out) {
+            DirParams D{};
+            D.inst = p->d_inst;
+            D.units = p->d_all_units;
+            D.groups = p->parity ? p->d_all_groups : nullptr;
+            D.n_groups = p->parity ? p->n_all_groups : 0;
+            D.perm = p->d_perm;
+            D.kappa = p->d_kappa;
+            D.seg_q = sq;
+            D.seg_w = w.seg_w;
+            D.xe = w.xe;
+            D.steps = seg_len(sg);
+            D.total_modes = p->total_modes;
+            D.total_k = p->total_k;
+            D.dH_out = dH_out;
+            D.dh_off = p->d_dh_off;
+            D.kperm = p->d_kperm;
+            MDX_CUDA(launch_dH_accumulate(D, p->n_all_units, s), "dL/dH accumulation");
+        }
         if (p->n_dir_units <= 0) return MDX_OK;
         DirParams D{};
         D.inst = p->d_inst;
@@ -1302,6 +1380,10 @@ extern "C" int mdx_grad(mdx_plan *p, const float *exc, const double *q0, const d
         if ((rc = run_segment(p, P, T, s))) return rc;
         if ((rc = direction(0, bq[0]))) return rc;
     }
+    if (dH_out)
+        MDX_CUDA(launch_dH_symmetrize(dH_out, p->d_dh_off, p->d_inst, p->d_dh_plates,
+                                      p->n_dh_plates, s),
+                 "dL/dH symmetrisation");
     GradEpilogue g{};
     g.inst = p->d_inst;
     g.n_inst = p->n_inst;
@@ -1397,6 +1479,62 @@ extern "C" int mdx_coeffs_vjp(int n, const double *lambda, double D, double T0, 
     if (ds0) *ds0 = a0;
     if (ds1) *ds1 = a1;
     return MDX_OK;
+}
+
+extern "C" int mdx_plan_set_coupling(mdx_plan *p, int i, const float *H, const float *dH) {
+    if (!p) return fail(MDX_ERR_ARG, "plan is NULL");
+    if (i < 0 || i >= p->n_inst) return fail(MDX_ERR_ARG, "instance %d outside the plan", i);
+    const InstDesc &d = p->inst[i];
+    if (d.grouped)
+        return fail(MDX_ERR_UNSUPPORTED, "instance %d shares a grouped coupling tensor", i);
+    if (d.kind != MDX_KIND_PLATE || d.M == 0)
+        return fail(MDX_ERR_ARG, "instance %d is not a plate with stress modes", i);
+    if (!H) return fail(MDX_ERR_ARG, "H is required");
+    const int N = d.N;
+    for (int which = 0; which < 2; ++which) {
+        const float *src = which == 0 ? H : dH;
+        if (!src) continue;
+        for (int k = 0; k < d.M; ++k) {
+            const float *Hk = src + (size_t)k * N * N;
+            float amax = 0.f;
+            for (size_t t = 0; t < (size_t)N * N; ++t) {
+                if (!std::isfinite(Hk[t]))
+                    return fail(MDX_ERR_NONFINITE, "instance %d: non-finite coupling entry", i);
+                amax = std::max(amax, std::fabs(Hk[t]));
+            }
+            for (int a = 0; a < N; ++a)
+                for (int b = a + 1; b < N; ++b)
+                    if (std::fabs(Hk[(size_t)a * N + b] - Hk[(size_t)b * N + a]) > 1e-5f * amax + 1e-30f)
+                        return fail(MDX_ERR_ARG, "instance %d: H[%d] is not symmetric", i, k);
+        }
+    }
+    if (p->parity) {
+        // the class layout stores only the class pattern: the new tensor must follow it
+        std::vector<int> cls(N);
+        for (int a = 0; a < 4; ++a)
+            for (int q = 0; q < d.ncls[a]; ++q) cls[p->h_perm[i][d.ocls[a] + q]] = a;
+        std::vector<int> kc(d.M);
+        for (const auto &it : p->h_items) {
+            if (it.inst != i) continue;
+            for (int ci = it.chunk0; ci < it.chunk1; ++ci) {
+                const ParityChunk &ch = p->h_chunks[ci];
+                for (int q = 0; q < ch.mc; ++q) kc[p->h_kperm[d.k_off + ch.kl0 + q]] = ch.c;
+            }
+        }
+        for (int k = 0; k < d.M; ++k) {
+            const float *Hk = H + (size_t)k * N * N;
+            float amax = 0.f;
+            for (size_t t = 0; t < (size_t)N * N; ++t) amax = std::max(amax, std::fabs(Hk[t]));
+            for (int x = 0; x < N; ++x)
+                for (int y = 0; y < N; ++y)
+                    if ((cls[x] ^ cls[y]) != kc[k] && std::fabs(Hk[(size_t)x * N + y]) > 1e-6f * amax)
+                        return fail(MDX_ERR_ARG,
+                                    "instance %d: H lies outside the plan's symmetry classes", i);
+        }
+    }
+    MDX_CUDA(cudaSetDevice(p->device), "cudaSetDevice");
+    MDX_CUDA(cudaDeviceSynchronize(), "synchronise");
+    return upload_coupling(p, i, H, d.has_dir ? dH : nullptr);
 }
 
 extern "C" int mdx_plan_group_work(const mdx_plan *p, double *bytes_per_step,

@@ -617,7 +617,7 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                             kahan_add(s0, c0, -eta * xi);
                             ka[0] = s0;
                             ka[1] = c0;
-                            if (d.has_dir && P.xe) {
+                            if ((d.has_dir || P.xe_all) && P.xe) {
                                 P.xe[((long long)t_loc * 2 + 0) * P.total_k + kk] = xi;
                                 P.xe[((long long)t_loc * 2 + 1) * P.total_k + kk] = eta;
                             }
@@ -773,7 +773,7 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                         kahan_add(s0, c0, -dv[0] * dv[1]);
                         ka[0] = s0;
                         ka[1] = c0;
-                        if (d.has_dir && P.xe) {
+                        if ((d.has_dir || P.xe_all) && P.xe) {
                             P.xe[((long long)t_loc * 2 + 0) * P.total_k + d.k_off + k] = dv[1];
                             P.xe[((long long)t_loc * 2 + 1) * P.total_k + d.k_off + k] = dv[0];
                         }

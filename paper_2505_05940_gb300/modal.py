@@ -83,7 +83,17 @@ class Simulator:
             out["status"] = status
         return out
 
-    def grad(self, steps, d_audio, K, ckpt, exc=None, want_status=False):
+    def dH_layout(self):
+        """Offsets of each plate's [M][N][N] block in the d_H output (plan
+        order, plates with stress modes only) and the total length."""
+        offs, tot = {}, 0
+        for i, (n, m) in enumerate(zip(self.plan.n_modes, self.plan.n_stress)):
+            if m > 0:
+                offs[i] = tot
+                tot += int(m) * int(n) * int(n)
+        return offs, tot
+
+    def grad(self, steps, d_audio, K, ckpt, exc=None, want_status=False, want_dH=False):
         dev = self.device
         exc = self._exc_for(steps) if exc is None else exc
         work = torch.empty(self.plan.workspace_bytes(steps, K) // 4 + 1, dtype=torch.float32,
@@ -96,6 +106,8 @@ class Simulator:
                    d_tau=torch.empty(self.n_inst, **f64),
                    d_kappa=torch.empty(max(1, self.kappa.numel()), **f64),
                    d_dir=torch.empty(self.n_inst, **f64))
+        if want_dH:
+            out["d_H"] = torch.empty(max(1, self.dH_layout()[1]), **f64)
         status = torch.empty(self.n_inst, dtype=torch.int32, device=dev) if want_status else None
         self.plan.grad(steps, d_audio.contiguous(), K, ckpt, work, exc=exc, out=out,
                        status=status)

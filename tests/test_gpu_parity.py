@@ -193,7 +193,7 @@ def test_gradients_match_oracle_adjoint(kind):
     K = 256
     r = sim.simulate(steps, K=K)
     g = sim.grad(steps, torch.tensor(ybar[None, :], dtype=torch.float32, device="cuda"), K,
-                 r["ckpt"], want_status=True)
+                 r["ckpt"], want_status=True, want_dH=(kind == "plate"))
     torch.cuda.synchronize()
     assert int(g["status"][0]) == 0
     adj = oracle.adjoint(oi, ybar, want_dH=(kind == "plate"))
@@ -212,6 +212,16 @@ def test_gradients_match_oracle_adjoint(kind):
             pass   # a struck plate starts at rest: still a valid comparison
         e = rel(got[name][:len(ref)], ref)
         assert e <= GTOL, (name, e)
+    if kind == "plate":
+        # full dL/dH (symmetrised); the class layout gives it on the class pattern
+        dHg = got["d_H"][:oi.M * oi.N * oi.N].reshape(oi.M, oi.N, oi.N)
+        ref = adj["dH"]
+        if layout == "classes":
+            fc, kc = classes_of(oi)
+            mask = (fc[:, None] ^ fc[None, :])[None] == kc[:, None, None]
+            assert np.all(dHg[~mask] == 0.0)
+            ref = np.where(mask, ref, 0.0)
+        assert rel(dHg, ref) <= GTOL, rel(dHg, ref)
 
 
 def test_gradients_independent_of_checkpoint_interval():
