@@ -186,6 +186,26 @@ int mdx_plan_set_coefficients(mdx_plan *plan, const double *omega2, const double
                               const double *kappa);
 
 /*
+ * Linear response of every instance of the plan, parallel in time (Sec.
+ * 4.3.2: the linear modes evolve by repeated multiplication with their
+ * discrete poles, evaluated as a prefix scan over time).  The nonlinear terms
+ * are dropped (tau' and kappa ignored); every mode follows the plan scheme's
+ * recursion q^{n+1} = g q^n + p q^{n-1} + r b e^n exactly (Eq. 20-23, or Eq.
+ * 15-19), written as X^{n+1} = A X^n + (r b e^n, 0) with the companion matrix
+ * A of the mode's poles.  Time is cut into chunks of 256 steps: each chunk's
+ * response to its own input from rest, then the chunk boundary states
+ * S_j = A^256 S_{j-1} + E_j, then every chunk again from its true state with
+ * the pickup.  FP64 arithmetic, FP32 audio.  Arguments as in mdx_simulate;
+ * work is caller-owned device scratch of mdx_linear_workspace_bytes(plan,
+ * steps).  Asynchronous on `stream`.  Errors: MDX_ERR_ARG (workspace, steps),
+ * MDX_ERR_CUDA.
+ */
+size_t mdx_linear_workspace_bytes(const mdx_plan *plan, int steps);
+int mdx_simulate_linear(mdx_plan *plan, const float *exc, const double *q0, const double *qm1,
+                        int steps, float *audio, double *q_end, double *qm1_end, void *work,
+                        size_t work_bytes, int *status, void *stream);
+
+/*
  * Replace the coupling tensor H (Eq. 10) of plate `inst` in a plan, and its
  * direction tensor dH if the plate was planned with one (dH NULL keeps it):
  * host FP32 [M][N][N], symmetric in the last two indices, read during the call

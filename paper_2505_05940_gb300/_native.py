@@ -30,7 +30,8 @@ EXPORTED = ("mdx_last_error", "mdx_version", "mdx_plan_create", "mdx_plan_destro
             "mdx_mlp_act_elems", "mdx_mlp_work_elems", "mdx_mlp_forward", "mdx_mlp_backward",
             "mdx_adam_step", "mdx_f32_to_bf16", "mdx_plan_set_l2_keep", "mdx_plan_l2_keep",
             "mdx_difference_coefficients", "mdx_coefficient_grads", "mdx_modal_from_physics",
-            "mdx_physics_vjp", "mdx_plan_group_work", "mdx_plan_set_coupling")
+            "mdx_physics_vjp", "mdx_plan_group_work", "mdx_plan_set_coupling",
+            "mdx_linear_workspace_bytes", "mdx_simulate_linear")
 
 
 class MdxError(RuntimeError):
@@ -139,6 +140,9 @@ def load(build_if_missing: bool = True):
                                      ctypes.c_double, ctypes.c_double, _D, _D, _D, _D, _D, _D, _D]
         L.mdx_plan_set_coefficients.argtypes = [vp, _D, _D, _D, _D, _D, _D]
         L.mdx_plan_set_coupling.argtypes = [vp, i32, _F, _F]
+        L.mdx_linear_workspace_bytes.argtypes = [vp, i32]
+        L.mdx_linear_workspace_bytes.restype = sz
+        L.mdx_simulate_linear.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, vp, sz, vp, vp]
         L.mdx_modal_from_physics.argtypes = [ctypes.POINTER(Physics), ctypes.POINTER(Modal)]
         L.mdx_physics_vjp.argtypes = [ctypes.POINTER(Physics), i32, i32, _D, _D,
                                       ctypes.c_double, _D, ctypes.c_double, _D,
@@ -359,6 +363,17 @@ class Plan:
         check(load().mdx_simulate(self._h, _ptr(exc), _ptr(q0), _ptr(qm1), int(steps),
                                   _ptr(audio), _ptr(q_end), _ptr(qm1_end), int(K), _ptr(ckpt),
                                   _ptr(status), _stream(stream)))
+
+    def simulate_linear(self, steps, work, exc=None, q0=None, qm1=None, audio=None, q_end=None,
+                        qm1_end=None, status=None, stream=None):
+        """Raw call of mdx_simulate_linear (device tensors allocated by the caller)."""
+        wb = work.numel() * work.element_size()
+        check(load().mdx_simulate_linear(self._h, _ptr(exc), _ptr(q0), _ptr(qm1), int(steps),
+                                         _ptr(audio), _ptr(q_end), _ptr(qm1_end), _ptr(work), wb,
+                                         _ptr(status), _stream(stream)))
+
+    def linear_workspace_bytes(self, steps):
+        return int(load().mdx_linear_workspace_bytes(self._h, steps))
 
     def grad(self, steps, d_audio, K, ckpt, work, exc=None, q0=None, qm1=None, out=None,
              status=None, stream=None):

@@ -286,7 +286,7 @@ __device__ __forceinline__ int reduce16_index(int lane) {
 
 struct Ctrl {
     uint64_t full[8], empty[8], conv[8];
-    uint64_t qready, mma_done, epi_free, drain;
+    uint64_t qready, mma_done[2], epi_free[2], drain;
     uint32_t tmem_base;
     int fail;            // set by any role that gave up; read by the epilogue warps
     int pad[2];
@@ -309,6 +309,9 @@ __global__ void __launch_bounds__(kGrpThreads, 1) group_kernel(const GroupParams
     float *ring = reinterpret_cast<float *>(smem + P.ring_off);
     float *lo = reinterpret_cast<float *>(smem + P.lo_off);
     float *qimg = reinterpret_cast<float *>(smem + P.q_off);
+    // this CTA's work units, cached in shared memory (every role walks them
+    // once per chunk)
+    GrpUnit *units = reinterpret_cast<GrpUnit *>(smem + P.scratch_off);
     volatile int *gabort = P.abort_flag;
 
     if (tid == 0) {
@@ -319,12 +322,16 @@ __global__ void __launch_bounds__(kGrpThreads, 1) group_kernel(const GroupParams
             bar_init(&C.conv[s], 2);
         }
         bar_init(&C.qready, 1);
-        bar_init(&C.mma_done, 1);
-        bar_init(&C.epi_free, 4);
+        for (int b = 0; b < 2; ++b) {
+            bar_init(&C.mma_done[b], 1);
+            bar_init(&C.epi_free[b], 4);
+        }
         bar_init(&C.drain, 1);
         C.fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    for (int x = tid; x < (u1 - u0) * (int)(sizeof(GrpUnit) / 4); x += kGrpThreads)
+        reinterpret_cast<int *>(units)[x] = reinterpret_cast<const int *>(P.units + u0)[x];
     if (warp == 1) {
         // the whole tensor memory of the SM (one CTA per SM)
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
@@ -352,7 +359,7 @@ __global__ void __launch_bounds__(kGrpThreads, 1) group_kernel(const GroupParams
             bool ok = true;
             for (int it = 0; it < steps && ok; ++it)
                 for (int u = u0; u < u1 && ok; ++u) {
-                    const GrpUnit &U = P.units[u];
+                    const GrpUnit &U = units[u - u0];
                     for (int t = 0; t < nt && ok; ++t) {
                         const long long off = U.off[t];
                         if (off < 0) continue;
@@ -395,9 +402,11 @@ __global__ void __launch_bounds__(kGrpThreads, 1) group_kernel(const GroupParams
                     break;
                 }
                 for (int u = u0; u < u1 && ok; ++u, ++ucount) {
-                    const GrpUnit &U = P.units[u];
-                    // the epilogue of the previous unit has read the accumulators
-                    if (!bar_wait(&C.epi_free, (uint32_t)((ucount & 1) ^ 1), P.wait_limit, gabort)) {
+                    const GrpUnit &U = units[u - u0];
+                    // two accumulator sets: the epilogue of the unit two back has read this one
+                    const int buf = (int)(ucount & 1);
+                    if (!bar_wait(&C.epi_free[buf], (uint32_t)(((ucount >> 1) & 1) ^ 1),
+                                  P.wait_limit, gabort)) {
                         ok = false;
                         break;
                     }
@@ -409,7 +418,7 @@ __global__ void __launch_bounds__(kGrpThreads, 1) group_kernel(const GroupParams
                         const uint32_t sbo_q = (uint32_t)(kp / 4) * 128u;
                         const uint32_t qa = su32(qimg + G.qoff[a]);
                         const uint32_t qla = su32(qimg + G.qoff[a] + Bp * kp);
-                        const uint32_t d = tmem + (uint32_t)(t * Bp);
+                        const uint32_t d = tmem + (uint32_t)((buf * nt + t) * Bp);
                         for (int j = 0; j < kp / kGrpChunk; ++j) {
                             if (!bar_wait(&C.conv[slot], ph, P.wait_limit, gabort)) {
                                 ok = false;
@@ -437,7 +446,7 @@ __global__ void __launch_bounds__(kGrpThreads, 1) group_kernel(const GroupParams
                             }
                         }
                     }
-                    if (ok) mma_commit(&C.mma_done);
+                    if (ok) mma_commit(&C.mma_done[buf]);
                 }
             }
             if (!ok) {
@@ -460,7 +469,7 @@ __global__ void __launch_bounds__(kGrpThreads, 1) group_kernel(const GroupParams
         bool ok = true;
         for (int it = 0; it < steps && ok; ++it)
             for (int u = u0; u < u1 && ok; ++u) {
-                const GrpUnit &U = P.units[u];
+                const GrpUnit &U = units[u - u0];
                 for (int t = 0; t < nt && ok; ++t) {
                     if (U.off[t] < 0) continue;
                     const int a = U.c ^ G.tile_sb[t];
@@ -508,11 +517,14 @@ __global__ void __launch_bounds__(kGrpThreads, 1) group_kernel(const GroupParams
         const int r = 32 * quarter + lane;     // accumulator row of this thread
         const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
         const unsigned nct = (unsigned)G.n_ctas;
+        const int fcol = 2 * nt * Bp;          // first column of the force accumulators
         const int slot_in_group = cta - G.cta0;
         unsigned *cnt = P.counters + gi;
         const long long TM = P.total_modes;
         long long ucount = 0;
         bool ok = true;
+        bool owner = false;
+        for (int b = 0; b < G.B; ++b) owner = owner || (P.plates[G.plate0 + b].owner == cta);
         // owners: initial q (class order) of the plates this CTA steps
         for (int b = 0; b < G.B; ++b) {
             const GrpPlate pl = P.plates[G.plate0 + b];
@@ -570,13 +582,16 @@ __global__ void __launch_bounds__(kGrpThreads, 1) group_kernel(const GroupParams
                 for (int i = 0; i < 16; ++i) z[i] = 0.f;
                 for (int t = 0; t < nt; ++t)
                     for (int cb = 0; cb < Bp; cb += 16)
-                        tmem_st16(tmem + lane_base + (uint32_t)((nt + t) * Bp + cb), z);
+                        tmem_st16(tmem + lane_base + (uint32_t)(fcol + t * Bp + cb), z);
                 tmem_wait_st();
             }
             // ---- stress modes of this CTA
             for (int u = u0; u < u1; ++u, ++ucount) {
-                const GrpUnit &U = P.units[u];
-                bool got = bar_wait(&C.mma_done, (uint32_t)(ucount & 1), P.wait_limit, gabort);
+                const GrpUnit &U = units[u - u0];
+                const int buf = (int)(ucount & 1);
+                const uint32_t dcol = (uint32_t)(buf * nt * Bp);
+                bool got = bar_wait(&C.mma_done[buf], (uint32_t)((ucount >> 1) & 1), P.wait_limit,
+                                    gabort);
                 if (!got) C.fail = 1;
                 epi_bar();
                 if (*reinterpret_cast<volatile int *>(&C.fail)) {
@@ -592,7 +607,7 @@ __global__ void __launch_bounds__(kGrpThreads, 1) group_kernel(const GroupParams
                     for (int t = 0; t < nt; ++t) {
                         if (U.off[t] < 0) continue;
                         float v[16];
-                        tmem_ld16(tmem + lane_base + (uint32_t)(t * Bp + cb), v);
+                        tmem_ld16(tmem + lane_base + dcol + (uint32_t)(t * Bp + cb), v);
                         const int sb = G.tile_sb[t];
                         if (r < G.tile_rows[t]) {
                             const int kp = G.kpad[sb];
@@ -621,17 +636,17 @@ __global__ void __launch_bounds__(kGrpThreads, 1) group_kernel(const GroupParams
                     if (U.off[t] < 0) continue;
                     for (int cb = 0; cb < Bp; cb += 16) {
                         float v[16], f[16];
-                        tmem_ld16(tmem + lane_base + (uint32_t)(t * Bp + cb), v);
-                        tmem_ld16(tmem + lane_base + (uint32_t)((nt + t) * Bp + cb), f);
+                        tmem_ld16(tmem + lane_base + dcol + (uint32_t)(t * Bp + cb), v);
+                        tmem_ld16(tmem + lane_base + (uint32_t)(fcol + t * Bp + cb), f);
 #pragma unroll
                         for (int i = 0; i < 16; ++i) f[i] = fmaf(C.ke[cb + i], v[i], f[i]);
-                        tmem_st16(tmem + lane_base + (uint32_t)((nt + t) * Bp + cb), f);
+                        tmem_st16(tmem + lane_base + (uint32_t)(fcol + t * Bp + cb), f);
                     }
                 }
                 tmem_wait_st();
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) bar_arrive(&C.epi_free);
+                if (lane == 0) bar_arrive(&C.epi_free[buf]);
             }
             if (!ok) break;
             // ---- partial forces of this CTA -> global slot (class order)
@@ -639,7 +654,7 @@ __global__ void __launch_bounds__(kGrpThreads, 1) group_kernel(const GroupParams
                 const int sb = G.tile_sb[t];
                 for (int cb = 0; cb < Bp; cb += 16) {
                     float f[16];
-                    tmem_ld16(tmem + lane_base + (uint32_t)((nt + t) * Bp + cb), f);
+                    tmem_ld16(tmem + lane_base + (uint32_t)(fcol + t * Bp + cb), f);
                     if (r < G.tile_rows[t]) {
                         const long long pos = G.ocls[sb] + G.tile_r0[t] + r;
 #pragma unroll
@@ -657,8 +672,6 @@ __global__ void __launch_bounds__(kGrpThreads, 1) group_kernel(const GroupParams
                 atomicAdd(cnt, 1u);
             }
             // ---- owners: gather the forces, step the plates, pickup, new q
-            bool owner = false;
-            for (int b = 0; b < G.B; ++b) owner = owner || (P.plates[G.plate0 + b].owner == cta);
             if (owner) {
                 if (!group_wait(nct * (unsigned)(2 + 2 * it))) {
                     ok = false;
@@ -944,9 +957,9 @@ int group_plan_build(GroupPlan **out, const mdx_instance *I, const std::vector<I
         image_members.push_back(mem);
     }
     // ---- kernel groups: members of an image in batches of at most Bsub plates
-    const int ring = 3;
     const int ctrl_bytes = (int)((sizeof(Ctrl) + 1023) & ~size_t(1023));
-    const int fixed = ctrl_bytes + 2 * ring * kGrpStageBytes;
+    const int min_ring = 4;   // at least this many stages beside the Q images
+    const int fixed = ctrl_bytes + 2 * min_ring * kGrpStageBytes;
     struct KG {
         int image;
         std::vector<int> plates;
@@ -957,9 +970,11 @@ int group_plan_build(GroupPlan **out, const mdx_instance *I, const std::vector<I
         int sumk = 0;
         for (int a = 0; a < 4; ++a) sumk += im.kpad[a];
         const int nt = (int)im.tile_sb.size();
-        int bsub = kGrpMaxB;
-        while (bsub > 16 && (2 * nt * bsub > 512 || fixed + 8LL * bsub * sumk > smem_optin)) bsub -= 16;
-        if (2 * nt * bsub > 512 || fixed + 8LL * bsub * sumk > smem_optin)
+        // two accumulator sets and the forces in tensor memory; the Q images and
+        // at least min_ring stages in shared memory
+        int bsub = 32;
+        while (bsub > 16 && (3 * nt * bsub > 512 || fixed + 8LL * bsub * sumk > smem_optin)) bsub -= 16;
+        if (3 * nt * bsub > 512 || fixed + 8LL * bsub * sumk > smem_optin)
             return bail(gfail(MDX_ERR_UNSUPPORTED, "grouped plate: modes exceed the shared-memory budget"));
         const std::vector<int> &mem = image_members[ii];
         const int nb = (int)((mem.size() + bsub - 1) / bsub);
@@ -1103,13 +1118,20 @@ int group_plan_build(GroupPlan **out, const mdx_instance *I, const std::vector<I
     gp->kap_floats = kap_off;
     gp->part_floats = part_off;
     gp->qbuf_floats = qbuf_off;
-    // shared memory: control block, ring, remainder ring, Q images
+    // shared memory: control block, ring, remainder ring, Q images, the CTA's
+    // work units; as many stages as fit (at most 8)
+    int max_units = 1;
+    for (size_t c = 0; c + 1 < gp->cta_units.size(); c += 2)
+        max_units = std::max(max_units, gp->cta_units[c + 1] - gp->cta_units[c]);
+    const int unit_bytes = (int)((max_units * sizeof(GrpUnit) + 127) & ~size_t(127));
+    const int ring = std::max(min_ring, std::min(8, (smem_optin - ctrl_bytes - q_floats_max * 4 -
+                                                     unit_bytes) / (2 * kGrpStageBytes)));
     gp->ring_stages = ring;
     gp->ring_off = ctrl_bytes;
     gp->lo_off = gp->ring_off + ring * kGrpStageBytes;
     gp->q_off = gp->lo_off + ring * kGrpStageBytes;
     gp->scratch_off = gp->q_off + q_floats_max * 4;
-    gp->smem = (size_t)gp->scratch_off;
+    gp->smem = (size_t)gp->scratch_off + unit_bytes;
     if ((int)gp->smem > smem_optin)
         return bail(gfail(MDX_ERR_UNSUPPORTED, "grouped plates exceed the shared-memory budget"));
     // kappa tables stay zero until group_plan_set_kappa

@@ -317,6 +317,25 @@ struct GroupParams {
     float l2_keep;
 };
 
+// Linear response parallel in time (mdx_linear.cu): chunks of kLinChunk steps.
+constexpr int kLinChunk = 256;
+struct LinearParams {
+    const InstDesc *inst;
+    int n_inst;
+    const int *mode_inst;           // [total_modes] instance of each mode
+    const double *omega2, *gamma, *dt, *b, *c;   // per mode FP64
+    int scheme;
+    int steps, total_steps, L, n_chunks;
+    const float *exc;               // [n_inst][total_steps] or nullptr
+    const double *q0, *qm1;         // [total_modes] or nullptr
+    float *audio;                   // [n_inst][total_steps] or nullptr
+    double *q_end, *qm1_end;        // [total_modes] or nullptr
+    double *E, *S;                  // [n_chunks][total_modes][2] each
+    long long total_modes;
+    int *status;
+};
+cudaError_t launch_linear(const LinearParams &P, cudaStream_t s);
+
 struct GroupPlan;   // host side of the grouped path (mdx_group.cu)
 // Builds the grouped path for the plates with grouped[i] != 0 (host FP32 H,
 // classes and kappa from the instance descriptions); fails with an MDX_ERR_*.

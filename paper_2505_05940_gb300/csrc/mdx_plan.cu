@@ -65,6 +65,8 @@ struct mdx_plan {
     InstDesc *d_inst = nullptr;
     ModeCoef coef{};
     double *d_omega2 = nullptr, *d_gamma = nullptr, *d_dt = nullptr;
+    double *d_b64 = nullptr, *d_c64 = nullptr;   // FP64 b, c (linear solver)
+    int *d_mode_inst = nullptr;                  // instance of each mode
     float *d_H = nullptr, *d_dH = nullptr, *d_kappa = nullptr;
     // plate work assignment
     int n_cta = 0;
@@ -440,6 +442,11 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
         if ((rc = upload(p, &p->d_omega2, w2d.data(), TM))) return bail(rc);
         if ((rc = upload(p, &p->d_gamma, gmd.data(), TM))) return bail(rc);
         if ((rc = upload(p, &p->d_dt, dtd.data(), TM))) return bail(rc);
+        if ((rc = upload(p, &p->d_b64, p->h_b.data(), TM))) return bail(rc);
+        if ((rc = upload(p, &p->d_c64, p->h_c.data(), TM))) return bail(rc);
+        std::vector<int> mi;
+        for (int i = 0; i < n_inst; ++i) mi.insert(mi.end(), (size_t)p->inst[i].N, i);
+        if ((rc = upload(p, &p->d_mode_inst, mi.data(), mi.size()))) return bail(rc);
     }
     // ---- tension list (strings, membranes and plates without coupling)
     for (int i = 0; i < n_inst; ++i) {
@@ -794,6 +801,10 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
             p->h_items = items;
             p->h_chunks = chunks;
             p->h_perm = perm;
+            // internal -> user stress index at each plate's k_off (the packing reads it)
+            p->h_kperm.assign(std::max<long long>(p->total_k, 1), 0);
+            for (int i = 0; i < n_inst; ++i)
+                for (int kk = 0; kk < p->inst[i].M; ++kk) p->h_kperm[p->inst[i].k_off + kk] = kperm[i][kk];
             for (int i = 0; i < n_inst; ++i) {
                 if (p->inst[i].M == 0) continue;
                 const int rcu = upload_coupling(p, i, I[i].H, I[i].dH);
@@ -819,11 +830,9 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
             // indexed by each plate's k_off (grouped plates keep their range, unused here)
             std::vector<float> kap2(std::max<long long>(p->total_k, 1), 0.f);
             std::vector<int> perm_all, kperm_all(std::max<long long>(p->total_k, 1), 0);
-            p->h_kperm.assign(std::max<long long>(p->total_k, 1), 0);
             for (int i = 0; i < n_inst; ++i) {
                 InstDesc &d = p->inst[i];
                 for (int kk = 0; kk < d.M; ++kk) {
-                    p->h_kperm[d.k_off + kk] = kperm[i][kk];
                     kap2[d.k_off + kk] = (float)I[i].kappa[kperm[i][kk]];
                     kperm_all[d.k_off + kk] = kperm[i][kk];
                 }
@@ -1537,6 +1546,59 @@ extern "C" int mdx_plan_set_coupling(mdx_plan *p, int i, const float *H, const f
     return upload_coupling(p, i, H, d.has_dir ? dH : nullptr);
 }
 
+extern "C" size_t mdx_linear_workspace_bytes(const mdx_plan *p, int steps) {
+    if (!p || steps <= 0) return 0;
+    const size_t nch = (size_t)((steps + kLinChunk - 1) / kLinChunk);
+    return 2 * nch * (size_t)p->total_modes * 2 * sizeof(double);
+}
+
+extern "C" int mdx_simulate_linear(mdx_plan *p, const float *exc, const double *q0,
+                                   const double *qm1, int steps, float *audio, double *q_end,
+                                   double *qm1_end, void *work, size_t work_bytes, int *status,
+                                   void *stream) {
+    if (!p) return fail(MDX_ERR_ARG, "plan is NULL");
+    if (steps < 0) return fail(MDX_ERR_ARG, "steps must be >= 0");
+    const size_t need = mdx_linear_workspace_bytes(p, steps);
+    if (steps > 0 && (!work || work_bytes < need))
+        return fail(MDX_ERR_ARG, "workspace of %zu bytes is smaller than the %zu bytes required",
+                    work_bytes, need);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    MDX_CUDA(cudaSetDevice(p->device), "cudaSetDevice");
+    if (status) MDX_CUDA(cudaMemsetAsync(status, 0, p->n_inst * sizeof(int), s), "memset status");
+    if (steps == 0) {
+        AuxInit a{q0, qm1, p->d_state, p->total_modes};
+        MDX_CUDA(launch_init_state(a, s), "init state");
+        MDX_CUDA(launch_finalize_state(p->d_state, p->total_modes, q_end, qm1_end, s), "finalize");
+        return MDX_OK;
+    }
+    LinearParams L{};
+    L.inst = p->d_inst;
+    L.n_inst = p->n_inst;
+    L.mode_inst = p->d_mode_inst;
+    L.omega2 = p->d_omega2;
+    L.gamma = p->d_gamma;
+    L.dt = p->d_dt;
+    L.b = p->d_b64;
+    L.c = p->d_c64;
+    L.scheme = p->scheme;
+    L.steps = steps;
+    L.total_steps = steps;
+    L.L = kLinChunk;
+    L.n_chunks = (steps + kLinChunk - 1) / kLinChunk;
+    L.exc = exc;
+    L.q0 = q0;
+    L.qm1 = qm1;
+    L.audio = audio;
+    L.q_end = q_end;
+    L.qm1_end = qm1_end;
+    L.E = static_cast<double *>(work);
+    L.S = L.E + (size_t)L.n_chunks * p->total_modes * 2;
+    L.total_modes = p->total_modes;
+    L.status = status;
+    MDX_CUDA(launch_linear(L, s), "linear solver");
+    return MDX_OK;
+}
+
 extern "C" int mdx_plan_group_work(const mdx_plan *p, double *bytes_per_step,
                                    double *flops_per_step) {
     if (!p) return fail(MDX_ERR_ARG, "plan is NULL");
@@ -1666,6 +1728,8 @@ extern "C" int mdx_plan_set_coefficients(mdx_plan *p, const double *omega2, cons
     MDX_CUDA(cudaMemcpy(dc + 7 * TM, cl.data(), TM * 4, cudaMemcpyHostToDevice), "upload");
     MDX_CUDA(cudaMemcpy(p->d_omega2, w2.data(), TM * 8, cudaMemcpyHostToDevice), "upload");
     MDX_CUDA(cudaMemcpy(p->d_gamma, gm.data(), TM * 8, cudaMemcpyHostToDevice), "upload");
+    MDX_CUDA(cudaMemcpy(p->d_b64, bb.data(), TM * 8, cudaMemcpyHostToDevice), "upload");
+    MDX_CUDA(cudaMemcpy(p->d_c64, cc.data(), TM * 8, cudaMemcpyHostToDevice), "upload");
     // tau lives in the instance table; kappa in internal (class-sorted) order
     for (int i = 0; i < p->n_inst; ++i) p->inst[i].taup = (p->inst[i].kind == MDX_KIND_TENSION) ? (float)tt[i] : 0.f;
     MDX_CUDA(cudaMemcpy(p->d_inst, p->inst.data(), p->inst.size() * sizeof(InstDesc), cudaMemcpyHostToDevice), "upload");

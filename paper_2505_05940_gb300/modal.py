@@ -83,6 +83,29 @@ class Simulator:
             out["status"] = status
         return out
 
+    def simulate_linear(self, steps, q0=None, qm1=None, exc=None, want_state=False,
+                        want_status=False):
+        """Linear response (nonlinear terms dropped), parallel in time."""
+        dev = self.device
+        exc = self._exc_for(steps) if exc is None else exc
+        audio = torch.empty(self.n_inst, steps, dtype=torch.float32, device=dev)
+        work = torch.empty(max(1, self.plan.linear_workspace_bytes(steps) // 8),
+                           dtype=torch.float64, device=dev)
+        out = dict(audio=audio)
+        q_end = qm1_end = status = None
+        if want_state:
+            q_end = torch.empty(self.total_modes, dtype=torch.float64, device=dev)
+            qm1_end = torch.empty_like(q_end)
+            out["q_end"], out["qm1_end"] = q_end, qm1_end
+        if want_status:
+            status = torch.empty(self.n_inst, dtype=torch.int32, device=dev)
+            out["status"] = status
+        q0 = self.q0.detach() if q0 is None else q0
+        qm1 = self.qm1.detach() if qm1 is None else qm1
+        self.plan.simulate_linear(steps, work, exc=exc, q0=q0, qm1=qm1, audio=audio,
+                                  q_end=q_end, qm1_end=qm1_end, status=status)
+        return out
+
     def dH_layout(self):
         """Offsets of each plate's [M][N][N] block in the d_H output (plan
         order, plates with stress modes only) and the total length."""
