@@ -89,12 +89,35 @@ __device__ __forceinline__ bool bar_try(uint64_t *b, uint32_t parity) {
     return ok != 0;
 }
 
+// Non-blocking test of a phase parity (no suspension of the thread).
+__device__ __forceinline__ bool bar_test(uint64_t *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // Bounded wait on a phase parity; false when the limit ran out or the launch
 // is aborting.
 __device__ bool bar_wait(uint64_t *b, uint32_t parity, long long limit, volatile int *abort_flag) {
     for (long long i = 0; i < limit; ++i) {
         if (bar_try(b, parity)) return true;
         if ((i & 1023) == 1023 && *abort_flag) return false;
+    }
+    return false;
+}
+
+// The same wait as a tight poll without suspension, for the ring hand-offs
+// whose latency sets the pipeline's throughput.
+__device__ bool bar_spin(uint64_t *b, uint32_t parity, long long limit, volatile int *abort_flag) {
+    for (long long i = 0; i < 64 * limit; ++i) {
+        if (bar_test(b, parity)) return true;
+        if ((i & 4095) == 4095 && *abort_flag) return false;
     }
     return false;
 }
@@ -367,7 +390,7 @@ __global__ void __launch_bounds__(kGrpThreads, 1) group_kernel(const GroupParams
                         const int r8 = (G.tile_rows[t] + 7) & ~7;
                         const uint32_t bytes = (uint32_t)r8 * kGrpChunk * 4u;
                         for (int j = 0; j < G.kpad[a] / kGrpChunk; ++j) {
-                            if (!bar_wait(&C.empty[slot], ph ^ 1u, P.wait_limit, gabort)) {
+                            if (!bar_spin(&C.empty[slot], ph ^ 1u, P.wait_limit, gabort)) {
                                 ok = false;
                                 break;
                             }
@@ -420,18 +443,21 @@ __global__ void __launch_bounds__(kGrpThreads, 1) group_kernel(const GroupParams
                         const uint32_t qla = su32(qimg + G.qoff[a] + Bp * kp);
                         const uint32_t d = tmem + (uint32_t)((buf * nt + t) * Bp);
                         for (int j = 0; j < kp / kGrpChunk; ++j) {
-                            if (!bar_wait(&C.conv[slot], ph, P.wait_limit, gabort)) {
+                            if (!bar_spin(&C.conv[slot], ph, P.wait_limit, gabort)) {
                                 ok = false;
                                 break;
                             }
                             tc_fence_after();
                             const uint32_t as = su32(ring + (size_t)slot * (kGrpStageBytes / 4));
                             const uint32_t als = su32(lo + (size_t)slot * (kGrpStageBytes / 4));
+                            // K-steps of 8 columns (two core matrices) within the chunk;
+                            // 8-row groups are kGrpChunk / 4 core matrices apart
+                            constexpr uint32_t sbo_a = (kGrpChunk / 4) * 128u;
 #pragma unroll
-                            for (int kk = 0; kk < 2; ++kk) {
-                                const uint64_t ad = smem_desc(as + kk * 256u, 128u, 512u);
-                                const uint64_t ald = smem_desc(als + kk * 256u, 128u, 512u);
-                                const uint32_t qo = (uint32_t)(j * 4 + kk * 2) * 128u;
+                            for (int kk = 0; kk < kGrpChunk / 8; ++kk) {
+                                const uint64_t ad = smem_desc(as + kk * 256u, 128u, sbo_a);
+                                const uint64_t ald = smem_desc(als + kk * 256u, 128u, sbo_a);
+                                const uint32_t qo = (uint32_t)(j * (kGrpChunk / 4) + kk * 2) * 128u;
                                 const uint64_t qd = smem_desc(qa + qo, 128u, sbo_q);
                                 const uint64_t qld = smem_desc(qla + qo, 128u, sbo_q);
                                 mma_tf32(d, ad, qd, idesc, (j | kk) ? 1u : 0u);
@@ -476,7 +502,7 @@ __global__ void __launch_bounds__(kGrpThreads, 1) group_kernel(const GroupParams
                     const int r8 = (G.tile_rows[t] + 7) & ~7;
                     const int n4 = r8 * kGrpChunk / 4;
                     for (int j = 0; j < G.kpad[a] / kGrpChunk; ++j) {
-                        if (!bar_wait(&C.full[slot], ph, P.wait_limit, gabort)) {
+                        if (!bar_spin(&C.full[slot], ph, P.wait_limit, gabort)) {
                             ok = false;
                             break;
                         }
@@ -1097,11 +1123,24 @@ int group_plan_build(GroupPlan **out, const mdx_instance *I, const std::vector<I
             gp->cta_units.push_back(unit0 + (int)((long long)nu * c / d.n_ctas));
             gp->cta_units.push_back(unit0 + (int)((long long)nu * (c + 1) / d.n_ctas));
         }
+        // owners: each plate's update costs about its mode count; largest first
+        // onto the least-loaded CTA of the group
+        std::vector<int> owner_of(d.B), order(d.B);
+        std::vector<long long> load(d.n_ctas, 0);
+        for (int b = 0; b < d.B; ++b) order[b] = b;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            return inst[kgs[g].plates[x]].N > inst[kgs[g].plates[y]].N;
+        });
+        for (int b : order) {
+            const int c = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            owner_of[b] = d.cta0 + c;
+            load[c] += inst[kgs[g].plates[b]].N;
+        }
         std::vector<int> kc, pi;
         for (int b = 0; b < d.B; ++b) {
             GrpPlate pl{};
             pl.inst = kgs[g].plates[b];
-            pl.owner = d.cta0 + b % d.n_ctas;
+            pl.owner = owner_of[b];
             gp->plates.push_back(pl);
             kc.push_back(I[pl.inst].n_psi);   // (the per-instance planner zeroes M)
             pi.push_back(pl.inst);
