@@ -420,6 +420,22 @@ def forward_workload(a):
     print(json.dumps(line), flush=True)
 
 
+def physical_gradients(sim, prepared, d_omega2, d_gamma, d_kappa, d_dir):
+    """dL/d(T0, D, aspect, sigma0, sigma1) of every plate through
+    mdx_physics_vjp, from the per-mode gradients of the adjoint."""
+    from paper_2505_05940_gb300 import _native, physics
+    off = sim.plan.mode_offset
+    koff = np.concatenate([[0], np.cumsum(sim.plan.n_stress)])
+    out = []
+    for i, p in enumerate(prepared):
+        n, m = len(p["omega2"]), int(sim.plan.n_stress[i])
+        g = _native.physics_vjp(physics.physics_struct(p), n, m, d_omega2[off[i]:off[i] + n],
+                                d_gamma[off[i]:off[i] + n], 0.0, d_kappa[koff[i]:koff[i + 1]],
+                                float(d_dir[i]), p.get("dzeta4"))
+        out.append({k: g[k] for k in ("d_T0", "d_D", "d_aspect", "d_sigma0", "d_sigma1")})
+    return out
+
+
 # ----------------------------------------------------------------- C ABI alone
 
 class _Cuda:
@@ -640,10 +656,13 @@ def main():
             loss = losses.multires_log_stft(audio, tgt_d).sum()
             loss.backward()
             res = [loss.detach().cpu()] + [getattr(sim, k).grad.cpu() for k in out_keys]
+            # the per-mode gradients mapped to the physical parameters (C ABI, host)
+            phys = physical_gradients(sim, init_p, *[r.numpy() for r in res[1:]])
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / a.steps
         e2e = {"value": units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h)}
+               "d2h_bytes_per_step": int(d2h),
+               "physical_gradients_plate0": phys[0]}
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:
         v, cores, desc = oracle_sample(a, os.cpu_count() or 1, 200)

@@ -554,6 +554,11 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
         // overfull shared-memory state falls back to longest-processing-time
         // assignment of explicit pieces.
         const int state_cap = 24 * 1024;   // 96 KB of item state per CTA at most
+        // shared-memory block of one item: its state arrays, then its stress
+        // modes' d kappa pairs and kappa, then (owner) its gradient sums
+        auto item_floats = [&](const InstDesc &d, int nk, bool owner) {
+            return narr * d.Npad + 3 * ((nk + 3) & ~3) + (owner ? 2 * GA_N * d.Npad : 0);
+        };
         double total = 0.0;
         long long total_kk = 0;
         for (int i = 0; i < n_inst; ++i) {
@@ -670,7 +675,7 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
         if (contiguous_ok) {
             for (int g = 0; g < G && contiguous_ok; ++g) {
                 int need = 0;
-                for (const Piece &q : per[g]) need += narr * p->inst[q.inst].Npad;
+                for (const Piece &q : per[g]) need += item_floats(p->inst[q.inst], q.k1 - q.k0, true);
                 if (need > state_cap) contiguous_ok = false;
             }
         }
@@ -699,7 +704,7 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
             std::vector<int> sfl(G, 0);
             for (const Piece &pc : pieces) {
                 const InstDesc &d = p->inst[pc.inst];
-                const int need = narr * d.Npad;
+                const int need = item_floats(d, pc.k1 - pc.k0, true);
                 int best = -1;
                 for (int g = 0; g < G; ++g) {
                     bool has = false;
@@ -743,7 +748,7 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
                 it.slot = (int)(std::find(cl.begin(), cl.end(), g) - cl.begin());
                 it.owner = (it.slot == 0) ? 1 : 0;
                 it.smem_state = soff;
-                soff += narr * d.Npad;
+                soff += item_floats(d, it.k1 - it.k0, it.owner != 0);
                 items.push_back(it);
                 p->npad_max = std::max(p->npad_max, d.Npad);
             }

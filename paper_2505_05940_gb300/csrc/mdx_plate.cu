@@ -166,6 +166,15 @@ __device__ __forceinline__ void fma4(float4 &acc, const float4 &h, float x) {
     acc.w = fmaf(h.w, x, acc.w);
 }
 
+// Per-item shared-memory block: the state arrays, then for the item's stress
+// modes [k0, k1): (d kappa sum, compensation) pairs and kappa, then (owner
+// items of a reverse launch) the per-mode gradient sums [GA_N][2][Npad].
+template <bool PAR>
+__device__ __forceinline__ float *item_kacc(float *st, int Np) {
+    return st + (PAR ? ST_NARR_FUSED : ST_NARR) * Np;
+}
+__device__ __forceinline__ int item_kr4(const PlateItem &it) { return ((it.k1 - it.k0) + 3) & ~3; }
+
 // R: right-hand sides of the H pass (1: forward / recompute; 2: reverse;
 // 3: fused reverse + recompute of the previous segment, class layout only).
 // PAR: coupling stored in symmetry-class chunks (see ParityChunk).
@@ -350,6 +359,23 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                 st[ST_RQLO * d.Npad + s] = in ? ck[TM + d.mode_off + s] : 0.f;
                 st[ST_RV * d.Npad + s] = in ? ck[2 * TM + d.mode_off + s] : 0.f;
                 st[ST_RVLO * d.Npad + s] = in ? ck[3 * TM + d.mode_off + s] : 0.f;
+            }
+        }
+        // kappa and the d kappa sums of the item's stress modes; the owner's
+        // gradient sums (reverse): kept in shared memory for the whole launch
+        float *kac = item_kacc<PAR>(st, d.Npad);
+        const int kr4 = item_kr4(item), nk = item.k1 - item.k0;
+        for (int q = tid; q < kr4; q += kPlateThreads) {
+            const bool in = q < nk;
+            kac[2 * kr4 + q] = in ? P.kappa[d.k_off + item.k0 + q] : 0.f;
+            kac[2 * q] = (in && reverse) ? P.kacc[2 * (d.k_off + item.k0 + q)] : 0.f;
+            kac[2 * q + 1] = (in && reverse) ? P.kacc[2 * (d.k_off + item.k0 + q) + 1] : 0.f;
+        }
+        if (reverse && item.owner) {
+            float *gac = kac + 3 * kr4;
+            for (int e = tid; e < 2 * GA_N * d.Npad; e += kPlateThreads) {
+                const int row = e / d.Npad, s = e - row * d.Npad;
+                gac[e] = (s < d.N) ? P.gacc[(long long)row * TM + d.mode_off + s] : 0.f;
             }
         }
     }
@@ -581,7 +607,9 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                         if (kact && c4 == 0) red[kl * 4 + dd] = v;
                     }
                     // slot 3: kappa of the stress mode, so the force loop reads shared memory only
-                    if (kact && c4 == 0) red[kl * 4 + 3] = P.kappa[d.k_off + ch.kl0 + kl];
+                    float *kac = item_kacc<PAR>(st, Np);
+                    const int kr4 = item_kr4(item);
+                    if (kact && c4 == 0) red[kl * 4 + 3] = kac[2 * kr4 + ch.kl0 + kl - item.k0];
                     consumer_bar();
                     // forces, per mode in class order (each thread owns distinct modes)
                     for (int mp = tid; mp < d.N; mp += kPlateThreads) {
@@ -608,19 +636,20 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                         if (reverse) st[ST_FLOC2 * Np + su] += fb;
                         if constexpr (FUSED) st[ST_RFLOC * Np + su] += fr;
                     }
-                    if (reverse && rev_on && tid == 0) {
-                        for (int q = 0; q < mc; ++q) {
-                            const long long kk = d.k_off + ch.kl0 + q;
-                            const float eta = red[q * 4 + 0], xi = red[q * 4 + 1];
-                            float *ka = P.kacc + 2 * kk;
-                            float s0 = ka[0], c0 = ka[1];
-                            kahan_add(s0, c0, -eta * xi);
-                            ka[0] = s0;
-                            ka[1] = c0;
-                            if ((d.has_dir || P.xe_all) && P.xe) {
-                                P.xe[((long long)t_loc * 2 + 0) * P.total_k + kk] = xi;
-                                P.xe[((long long)t_loc * 2 + 1) * P.total_k + kk] = eta;
-                            }
+                    if (reverse && rev_on && tid < mc) {
+                        // one thread per stress mode of the chunk; the sums stay in
+                        // shared memory until the end of the launch
+                        const int q = tid;
+                        const long long kk = d.k_off + ch.kl0 + q;
+                        const float eta = red[q * 4 + 0], xi = red[q * 4 + 1];
+                        float *ka = kac + 2 * (ch.kl0 + q - item.k0);
+                        float s0 = ka[0], c0 = ka[1];
+                        kahan_add(s0, c0, -eta * xi);
+                        ka[0] = s0;
+                        ka[1] = c0;
+                        if ((d.has_dir || P.xe_all) && P.xe) {
+                            P.xe[((long long)t_loc * 2 + 0) * P.total_k + kk] = xi;
+                            P.xe[((long long)t_loc * 2 + 1) * P.total_k + kk] = eta;
                         }
                     }
                     consumer_bar();
@@ -749,7 +778,9 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                         for (int w = 0; w < kPlateWarps; ++w) a += red[(kk * 4 + dd) * kPlateWarps + w];
                         dv[dd] = a;
                     }
-                    const float kap = P.kappa[d.k_off + k];
+                    float *kac = item_kacc<PAR>(st, Np);
+                    const int kr4 = item_kr4(item);
+                    const float kap = kac[2 * kr4 + k - item.k0];
 #pragma unroll
                     for (int j = 0; j < kMaxSpt; ++j) {
                         const int sj = tid + j * kPlateThreads;
@@ -768,7 +799,7 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                     }
                     if (reverse && tid == 0) {
                         // d kappa_k -= eta xi ; directional derivative
-                        float *ka = P.kacc + 2 * (d.k_off + k);
+                        float *ka = kac + 2 * (k - item.k0);
                         float s0 = ka[0], c0 = ka[1];
                         kahan_add(s0, c0, -dv[0] * dv[1]);
                         ka[0] = s0;
@@ -858,14 +889,15 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                         const float vn = P.seg_v[(long long)t_loc * TM + m];
                         const float qn1 = P.seg_q[(long long)(t_loc + 1) * TM + m];
                         const float ybn = P.ybar[(long long)item.inst * P.total_steps + n];
-                        float *g = P.gacc;
+                        // the owner's gradient sums, in shared memory for the launch
+                        float *g = item_kacc<PAR>(st, Np) + 3 * item_kr4(item);
                         float gsum, gcmp;
 #define MDX_ACC(IDX, X)                                                    \
-    gsum = g[(long long)(2 * (IDX)) * TM + m];                             \
-    gcmp = g[(long long)(2 * (IDX) + 1) * TM + m];                         \
+    gsum = g[(2 * (IDX)) * Np + s];                                        \
+    gcmp = g[(2 * (IDX) + 1) * Np + s];                                    \
     kahan_add(gsum, gcmp, (X));                                            \
-    g[(long long)(2 * (IDX)) * TM + m] = gsum;                             \
-    g[(long long)(2 * (IDX) + 1) * TM + m] = gcmp;
+    g[(2 * (IDX)) * Np + s] = gsum;                                        \
+    g[(2 * (IDX) + 1) * Np + s] = gcmp;
                         MDX_ACC(GA_A, a * qn)
                         MDX_ACC(GA_V, a * vn)
                         MDX_ACC(GA_F, a * fmaf(b, e, -fB))
@@ -951,10 +983,25 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                     P.adj[m] = st[ST_QHI * Np + s];
                     P.adj[TM + m] = st[ST_QLO * Np + s];
                     P.adj[2 * TM + m] = st[ST_V * Np + s];
+                    const float *g = item_kacc<PAR>(st, Np) + 3 * item_kr4(item);
+#pragma unroll
+                    for (int row = 0; row < 2 * GA_N; ++row) P.gacc[(long long)row * TM + m] = g[row * Np + s];
                     if constexpr (FUSED) {
                         P.rseg_q[(long long)P.steps * TM + m] = st[ST_RQHI * Np + s];
                         P.rseg_v[(long long)P.steps * TM + m] = st[ST_RV * Np + s];
                     }
+                }
+            }
+        }
+        // every item's d kappa sums (its own stress-mode range)
+        if (reverse) {
+            for (int ii = it0; ii < it1; ++ii) {
+                const PlateItem item = P.items[ii];
+                const InstDesc d = P.inst[item.inst];
+                const float *kac = item_kacc<PAR>(S.state + item.smem_state, d.Npad);
+                for (int q = tid; q < item.k1 - item.k0; q += kPlateThreads) {
+                    P.kacc[2 * (d.k_off + item.k0 + q)] = kac[2 * q];
+                    P.kacc[2 * (d.k_off + item.k0 + q) + 1] = kac[2 * q + 1];
                 }
             }
         }

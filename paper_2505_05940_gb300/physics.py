@@ -28,8 +28,9 @@ def rectangle_sides(inst):
     return _coupling.sides(inst.area, inst.aspect)
 
 
-def physics_of(inst, fs, zeta4=None, omega_dt_max=OMEGA_T_LIMIT, **override):
-    """mdx_physics of one workload instance (override replaces fields)."""
+def physics_args(inst, fs, zeta4=None, omega_dt_max=OMEGA_T_LIMIT, **override):
+    """Fields of the mdx_physics of one workload instance (a plain dict that
+    pickles; override replaces fields)."""
     plate = inst.kind == "plate"
     ts = 0.0
     if inst.nonlinear and inst.kind == "string":
@@ -44,9 +45,19 @@ def physics_of(inst, fs, zeta4=None, omega_dt_max=OMEGA_T_LIMIT, **override):
                 sigma1=inst.sigma1, strike=inst.strike, pickup=inst.pickup,
                 tension_stiffness=ts,
                 vk_scale=inst.E / (2.0 * inst.rho_vol) if (plate and inst.nonlinear) else 0.0,
-                zeta4=zeta4)
+                zeta4=None if zeta4 is None else np.asarray(zeta4, np.float64))
     args.update(override)
-    return _native.physics_struct(**args)
+    return args
+
+
+def physics_of(inst, fs, zeta4=None, omega_dt_max=OMEGA_T_LIMIT, **override):
+    """mdx_physics of one workload instance (override replaces fields)."""
+    return _native.physics_struct(**physics_args(inst, fs, zeta4, omega_dt_max, **override))
+
+
+def physics_struct(prepared):
+    """mdx_physics of a prepared instance (for mdx_physics_vjp)."""
+    return _native.physics_struct(**prepared["physics_args"])
 
 
 def mode_labels(inst, n, fs=44100.0):
@@ -81,11 +92,12 @@ class PreparedInstance(dict):
 
 def prepare(inst, fs, steps, coupling="auto", want_aspect_derivative=False):
     """Physical parameters -> dict with the mdx_instance fields, the excitation
-    e [steps], the initial state q0, qm1 and bookkeeping (labels, lambda, and
-    for plates zeta4, the mdx_physics description `physics`)."""
+    e [steps], the initial state q0, qm1 and bookkeeping (labels, lambda, for
+    plates zeta4, and `physics_args`, the fields of the mdx_physics
+    description, see physics_struct)."""
     T = 1.0 / fs
-    ph = physics_of(inst, fs)
-    mod = _native.modal_from_physics(ph)
+    pargs = physics_args(inst, fs)
+    mod = _native.modal_from_physics(_native.physics_struct(**pargs))
     labels, lam = mod["labels"], mod["lam"]
     n_eff = len(lam)
     if inst.kind == "string":
@@ -124,14 +136,14 @@ def prepare(inst, fs, steps, coupling="auto", want_aspect_derivative=False):
             out["psi_class"] = psi_cls
         zeta4 = np.asarray(zeta4, np.float64)
         # kappa of Eq. 9 for the kept stress modes (second call, with zeta^4)
-        ph = physics_of(inst, fs, zeta4=np.concatenate([zeta4, np.full(inst.n_psi - M, 1.0)]))
-        out["kappa"] = _native.modal_from_physics(ph)["kappa"]
+        pargs = physics_args(inst, fs, zeta4=np.concatenate([zeta4, np.full(inst.n_psi - M, 1.0)]))
+        out["kappa"] = _native.modal_from_physics(_native.physics_struct(**pargs))["kappa"]
         out["H"] = H.astype(np.float32)
         out["zeta4"] = zeta4
         if dH is not None:
             out["dH"] = dH.astype(np.float32)
             out["dzeta4"] = dz
-    out["physics"] = ph
+    out["physics_args"] = pargs
     return out
 
 

@@ -51,7 +51,7 @@ def test_physical_gradients_match_oracle_finite_differences():
                  r["ckpt"], want_status=True)
     torch.cuda.synchronize()
     assert int(g["status"][0]) == 0
-    got = N.physics_vjp(p["physics"], 48, 12, g["d_omega2"].cpu().numpy(),
+    got = N.physics_vjp(physics.physics_struct(p), 48, 12, g["d_omega2"].cpu().numpy(),
                         g["d_gamma"].cpu().numpy(), 0.0, g["d_kappa"].cpu().numpy(),
                         float(g["d_dir"][0]), p["dzeta4"])
 
