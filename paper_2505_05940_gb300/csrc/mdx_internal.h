@@ -94,6 +94,9 @@ struct PlateItem {
     int owner;          // 1: this CTA writes audio / state / gradients of the instance
     int smem_state;     // float offset of this item's state block in shared memory
     int chunk0, chunk1; // parity layout: the item's class chunks
+    int cache;          // 1: per-mode coefficients, class permutation and (owner)
+                        // gradient sums are kept in the item's shared-memory block
+    int pad;
 };
 
 // Shared-memory state block of one item (floats, each of length Npad).

@@ -556,8 +556,13 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
         const int state_cap = 24 * 1024;   // 96 KB of item state per CTA at most
         // shared-memory block of one item: its state arrays, then its stress
         // modes' d kappa pairs and kappa, then (owner) its gradient sums
+        // (+ the per-mode coefficients and the class permutation, 8 arrays, and the
+        // owner's gradient sums, when the item caches them: plates up to 512 modes)
+        auto item_cached = [&](const InstDesc &d) { return d.Npad <= 512; };
         auto item_floats = [&](const InstDesc &d, int nk, bool owner) {
-            return narr * d.Npad + 3 * ((nk + 3) & ~3) + (owner ? 2 * GA_N * d.Npad : 0);
+            const bool c = item_cached(d);
+            return narr * d.Npad + 3 * ((nk + 3) & ~3) +
+                   (c ? 8 * d.Npad + (owner ? 2 * GA_N * d.Npad : 0) : 0);
         };
         double total = 0.0;
         long long total_kk = 0;
@@ -748,6 +753,7 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
                 it.slot = (int)(std::find(cl.begin(), cl.end(), g) - cl.begin());
                 it.owner = (it.slot == 0) ? 1 : 0;
                 it.smem_state = soff;
+                it.cache = item_cached(d) ? 1 : 0;
                 soff += item_floats(d, it.k1 - it.k0, it.owner != 0);
                 items.push_back(it);
                 p->npad_max = std::max(p->npad_max, d.Npad);

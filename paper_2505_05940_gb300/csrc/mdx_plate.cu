@@ -167,13 +167,27 @@ __device__ __forceinline__ void fma4(float4 &acc, const float4 &h, float x) {
 }
 
 // Per-item shared-memory block: the state arrays, then for the item's stress
-// modes [k0, k1): (d kappa sum, compensation) pairs and kappa, then (owner
-// items of a reverse launch) the per-mode gradient sums [GA_N][2][Npad].
+// modes [k0, k1): (d kappa sum, compensation) pairs and kappa, then the
+// per-mode coefficients [ITEM_NCOEF][Npad] and the class permutation [Npad],
+// then (owner items of a reverse launch) the gradient sums [GA_N][2][Npad].
 template <bool PAR>
 __device__ __forceinline__ float *item_kacc(float *st, int Np) {
     return st + (PAR ? ST_NARR_FUSED : ST_NARR) * Np;
 }
 __device__ __forceinline__ int item_kr4(const PlateItem &it) { return ((it.k1 - it.k0) + 3) & ~3; }
+enum ItemCoef : int { IC_EPS = 0, IC_RW2, IC_RW2LO, IC_R, IC_B, IC_C, IC_CLO, ITEM_NCOEF };
+template <bool PAR>
+__device__ __forceinline__ float *item_coef(float *st, int Np, const PlateItem &it) {
+    return item_kacc<PAR>(st, Np) + 3 * item_kr4(it);
+}
+template <bool PAR>
+__device__ __forceinline__ int *item_perm(float *st, int Np, const PlateItem &it) {
+    return reinterpret_cast<int *>(item_coef<PAR>(st, Np, it) + ITEM_NCOEF * Np);
+}
+template <bool PAR>
+__device__ __forceinline__ float *item_gacc(float *st, int Np, const PlateItem &it) {
+    return item_coef<PAR>(st, Np, it) + (ITEM_NCOEF + 1) * Np;
+}
 
 // R: right-hand sides of the H pass (1: forward / recompute; 2: reverse;
 // 3: fused reverse + recompute of the previous segment, class layout only).
@@ -371,8 +385,24 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
             kac[2 * q] = (in && reverse) ? P.kacc[2 * (d.k_off + item.k0 + q)] : 0.f;
             kac[2 * q + 1] = (in && reverse) ? P.kacc[2 * (d.k_off + item.k0 + q) + 1] : 0.f;
         }
-        if (reverse && item.owner) {
-            float *gac = kac + 3 * kr4;
+        if (item.cache) {
+            float *cf = item_coef<PAR>(st, d.Npad, item);
+            int *pm = item_perm<PAR>(st, d.Npad, item);
+            for (int s = tid; s < d.Npad; s += kPlateThreads) {
+                const bool in = s < d.N;
+                const long long m = d.mode_off + s;
+                cf[IC_EPS * d.Npad + s] = in ? P.coef.eps[m] : 0.f;
+                cf[IC_RW2 * d.Npad + s] = in ? P.coef.rw2[m] : 0.f;
+                cf[IC_RW2LO * d.Npad + s] = in ? P.coef.rw2lo[m] : 0.f;
+                cf[IC_R * d.Npad + s] = in ? P.coef.r[m] : 0.f;
+                cf[IC_B * d.Npad + s] = in ? P.coef.b[m] : 0.f;
+                cf[IC_C * d.Npad + s] = in ? P.coef.c[m] : 0.f;
+                cf[IC_CLO * d.Npad + s] = in ? P.coef.clo[m] : 0.f;
+                pm[s] = (PAR && in) ? P.perm[d.perm_off + s] : s;
+            }
+        }
+        if (reverse && item.owner && item.cache) {
+            float *gac = item_gacc<PAR>(st, d.Npad, item);
             for (int e = tid; e < 2 * GA_N * d.Npad; e += kPlateThreads) {
                 const int row = e / d.Npad, s = e - row * d.Npad;
                 gac[e] = (s < d.N) ? P.gacc[(long long)row * TM + d.mode_off + s] : 0.f;
@@ -414,7 +444,9 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                 } else {
                     const bool live = in && rev_on;
                     const float qn = live ? P.seg_q[(long long)t_loc * TM + m] : 0.f;
-                    const float wv = live ? P.coef.r[m] * st[ST_QHI * Np + s] : 0.f;
+                    const float rr = item.cache ? item_coef<PAR>(st, Np, item)[IC_R * Np + s]
+                                                : (live ? P.coef.r[m] : 0.f);
+                    const float wv = live ? rr * st[ST_QHI * Np + s] : 0.f;
                     st[ST_SRC0 * Np + s] = qn;
                     st[ST_SRC1 * Np + s] = wv;
                     if (live && item.owner && P.seg_w) P.seg_w[(long long)t_loc * TM + m] = wv;
@@ -440,7 +472,7 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                 const int Np = d.Npad;
                 const float *q = reverse ? st + ST_SRC0 * Np : st + ST_QHI * Np;
                 for (int mp = tid; mp < d.N; mp += kPlateThreads) {
-                    const int su = P.perm[d.perm_off + mp];
+                    const int su = item.cache ? item_perm<PAR>(st, Np, item)[mp] : P.perm[d.perm_off + mp];
                     st[ST_QP * Np + mp] = q[su];
                     if (reverse) st[ST_WP * Np + mp] = st[ST_SRC1 * Np + su];
                     if constexpr (FUSED) st[ST_RQP * Np + mp] = st[ST_RQHI * Np + su];
@@ -612,8 +644,9 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                     if (kact && c4 == 0) red[kl * 4 + 3] = kac[2 * kr4 + ch.kl0 + kl - item.k0];
                     consumer_bar();
                     // forces, per mode in class order (each thread owns distinct modes)
+                    const int *pmc = item.cache ? item_perm<PAR>(st, Np, item) : P.perm + d.perm_off;
                     for (int mp = tid; mp < d.N; mp += kPlateThreads) {
-                        const int su = P.perm[d.perm_off + mp];
+                        const int su = pmc[mp];
                         float fa = 0.f, fb = 0.f, fr = 0.f;
 #pragma unroll 4
                         for (int q = 0; q < mc; ++q) {
@@ -873,9 +906,15 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                     if (reverse) fB = st[ST_FLOC2 * Np + s];
                     if constexpr (FUSED) fR = st[ST_RFLOC * Np + s];
                 }
-                const float eps = P.coef.eps[m], rw2 = P.coef.rw2[m], r = P.coef.r[m];
-                const float rw2l = P.coef.rw2lo[m];
-                const float b = P.coef.b[m], c = P.coef.c[m], clo = P.coef.clo[m];
+                // cached: [coef][Np] in shared memory; else the plan's global arrays
+                const float *cf = item.cache ? item_coef<PAR>(st, Np, item) : nullptr;
+                const float eps = cf ? cf[IC_EPS * Np + s] : P.coef.eps[m];
+                const float rw2 = cf ? cf[IC_RW2 * Np + s] : P.coef.rw2[m];
+                const float r = cf ? cf[IC_R * Np + s] : P.coef.r[m];
+                const float rw2l = cf ? cf[IC_RW2LO * Np + s] : P.coef.rw2lo[m];
+                const float b = cf ? cf[IC_B * Np + s] : P.coef.b[m];
+                const float c = cf ? cf[IC_C * Np + s] : P.coef.c[m];
+                const float clo = cf ? cf[IC_CLO * Np + s] : P.coef.clo[m];
                 float x0 = st[ST_QHI * Np + s], x1 = st[ST_QLO * Np + s], x2 = st[ST_V * Np + s];
                 float x3 = st[ST_VLO * Np + s];
                 if (!reverse) {
@@ -890,14 +929,16 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                         const float qn1 = P.seg_q[(long long)(t_loc + 1) * TM + m];
                         const float ybn = P.ybar[(long long)item.inst * P.total_steps + n];
                         // the owner's gradient sums, in shared memory for the launch
-                        float *g = item_kacc<PAR>(st, Np) + 3 * item_kr4(item);
+                        // the owner's gradient sums: shared memory when cached
+                        float *g = item.cache ? item_gacc<PAR>(st, Np, item) + s : P.gacc + m;
+                        const long long gst = item.cache ? (long long)Np : TM;
                         float gsum, gcmp;
 #define MDX_ACC(IDX, X)                                                    \
-    gsum = g[(2 * (IDX)) * Np + s];                                        \
-    gcmp = g[(2 * (IDX) + 1) * Np + s];                                    \
+    gsum = g[(2 * (IDX)) * gst];                                           \
+    gcmp = g[(2 * (IDX) + 1) * gst];                                       \
     kahan_add(gsum, gcmp, (X));                                            \
-    g[(2 * (IDX)) * Np + s] = gsum;                                        \
-    g[(2 * (IDX) + 1) * Np + s] = gcmp;
+    g[(2 * (IDX)) * gst] = gsum;                                           \
+    g[(2 * (IDX) + 1) * gst] = gcmp;
                         MDX_ACC(GA_A, a * qn)
                         MDX_ACC(GA_V, a * vn)
                         MDX_ACC(GA_F, a * fmaf(b, e, -fB))
@@ -983,9 +1024,12 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                     P.adj[m] = st[ST_QHI * Np + s];
                     P.adj[TM + m] = st[ST_QLO * Np + s];
                     P.adj[2 * TM + m] = st[ST_V * Np + s];
-                    const float *g = item_kacc<PAR>(st, Np) + 3 * item_kr4(item);
+                    if (item.cache) {
+                        const float *g = item_gacc<PAR>(st, Np, item);
 #pragma unroll
-                    for (int row = 0; row < 2 * GA_N; ++row) P.gacc[(long long)row * TM + m] = g[row * Np + s];
+                        for (int row = 0; row < 2 * GA_N; ++row)
+                            P.gacc[(long long)row * TM + m] = g[row * Np + s];
+                    }
                     if constexpr (FUSED) {
                         P.rseg_q[(long long)P.steps * TM + m] = st[ST_RQHI * Np + s];
                         P.rseg_v[(long long)P.steps * TM + m] = st[ST_RV * Np + s];

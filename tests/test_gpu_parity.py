@@ -334,3 +334,25 @@ def test_autotuner_picks_a_fitting_stage_and_keeps_parity(tmp_path):
     torch.cuda.synchronize()
     ref = oracle.forward(oi)["y"]
     assert rel(r["audio"].cpu().numpy()[0], ref) <= TOL
+
+
+def test_set_coupling_equals_a_fresh_plan():
+    """mdx_plan_set_coupling repacks a new H into a live plan (dense and class
+    layouts): the next run equals a plan created with that H."""
+    fs, steps = 44100.0, 600
+    oi, _ = _grad_case("plate", 41, steps)
+    rng = np.random.default_rng(9)
+    for layout in ("dense", "classes"):
+        d = to_plan(oi, fs, layout)
+        sim = modal.Simulator([d])
+        H2 = oi.H * (1.0 + 0.05 * rng.standard_normal(oi.H.shape))
+        H2 = 0.5 * (H2 + H2.transpose(0, 2, 1))
+        if layout == "classes":
+            fc, kc = classes_of(oi)
+            H2 = H2 * ((fc[:, None] ^ fc[None, :])[None] == kc[:, None, None])
+        sim.plan.set_coupling(0, H2.astype(np.float32))
+        a = sim.simulate(steps)["audio"].cpu().numpy()
+        d2 = dict(d)
+        d2["H"] = H2.astype(np.float32)
+        b = modal.Simulator([d2]).simulate(steps)["audio"].cpu().numpy()
+        assert np.array_equal(a, b), layout
