@@ -137,7 +137,12 @@ typedef struct mdx_options {
                           arrival, so the other contributors' bounded waits run out and the
                           call reports MDX_ERR_TIMEOUT (fault-path tests);
                           bit 1: run the gradient as separate recompute and reverse launches
-                          instead of the fused sweep (equivalence tests); 0 in normal use */
+                          instead of the fused sweep (equivalence tests);
+                          bit 2: keep no per-plate coefficients or gradient sums in the plate
+                          kernel's shared memory (the path of plates too large for it;
+                          equivalence tests);
+                          bit 3: run the direction contraction on the CUDA-core kernel instead
+                          of the tensor cores (equivalence tests); 0 in normal use */
     int scheme;        /* MDX_SCHEME_SV (default) or MDX_SCHEME_TF */
     int group_engine;  /* plates with geom_group > 0: MDX_GROUP_TF32X3 (default) steps each
                           group with one shared coupling tensor on the tensor cores;

@@ -21,7 +21,9 @@
 // dL/dH^k_ij = -kappa_k (G_k + G_k^T)_ij / 2, since H^k is symmetric.
 #include <cuda_runtime.h>
 
+#include "../../include/mdx.h"
 #include "mdx_common.cuh"
+#include "mdx_tc.cuh"
 
 namespace mdx {
 
@@ -325,7 +327,316 @@ __global__ void __launch_bounds__(kDirThreads) dir_class_kernel(const DirParams 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core contraction (class layout).
+//
+// The contraction is reordered so that its inner product runs over the
+// columns s of the coupling block:
+//   <dH^k_ab, G_k> = sum_n xi_k^n (q_a^n . U^n_k) + eta_k^n (w_a^n . U^n_k),
+//   U^n_k = dH^k_ab q_b^n,
+// and all U for a tile of 128 steps and a chunk of (stress mode, row) pairs
+// form one GEMM
+//   D[n][(k, p)] = sum_s q_b^n[s] dH^k[p][s]      (M = 128 steps, K = s)
+// on tcgen05 (kind::tf32, split TF32 as in the grouped plate kernel: both
+// operands split into a round-to-nearest TF32 part and the FP32 remainder,
+// three products, error about 2^-21 of |dH||q|).  The epilogue reads D from
+// tensor memory, one step per lane: each thread forms q_a^n . U and
+// w_a^n . U for its step over the chunk's 16 rows p and accumulates
+// xi_k^n (.) + eta_k^n (.) per stress mode.  Columns of D are k-major
+// (column = 16 k + p), so a 16-column tensor-memory load holds one stress
+// mode's 16 rows.  One CTA per (plate, stress class c, row class a); the
+// stages run in order (operand staging by all threads, the MMAs by one
+// thread, then the epilogue by all eight warps, two per lane quarter).
+namespace {
+
+constexpr int kTcThreads = 256;
+constexpr int kTcM = 128;          // steps per tile (MMA M, tensor-memory lanes)
+constexpr int kTcP = 16;           // rows p per chunk
+constexpr int kTcQ = 16;           // stress modes per chunk
+constexpr int kTcRs = kTcM + 1;    // row stride of the q_a / w_a tiles
+constexpr int kTcXs = kTcQ + 1;    // row stride of the xi / eta tiles
+constexpr int kTcCtrl = 1024;      // control block at the start of shared memory
+constexpr long long kTcWait = 1LL << 22;
+
+struct DirTcCtrl {
+    uint64_t mma_bar;
+    uint32_t tmem;
+    int fail;
+    long long boff[kTcQ];   // float offset of each stress mode's class-a row 0
+    int rstride[kTcQ];      // floats between its rows
+    int kk[kTcQ];           // global stress index
+    float red[kTcThreads / 32][kTcQ / 2];
+};
+static_assert(sizeof(DirTcCtrl) <= kTcCtrl, "control block");
+
+__host__ __device__ inline size_t tc_align(size_t x) { return (x + 127) & ~(size_t)127; }
+
+struct TcLayout {
+    size_t ahi, alo, bhi, blo, qa, wa, xi, et, cols, end;
+};
+
+__host__ __device__ inline TcLayout tc_layout(int kc, int nmax) {
+    TcLayout L;
+    size_t o = kTcCtrl;
+    L.ahi = o; o = tc_align(o + (size_t)kTcM * kc * 4);
+    L.alo = o; o = tc_align(o + (size_t)kTcM * kc * 4);
+    L.bhi = o; o = tc_align(o + (size_t)nmax * kc * 4);
+    L.blo = o; o = tc_align(o + (size_t)nmax * kc * 4);
+    L.qa = o; o = tc_align(o + (size_t)kTcP * kTcRs * 4);
+    L.wa = o; o = tc_align(o + (size_t)kTcP * kTcRs * 4);
+    L.xi = o; o = tc_align(o + (size_t)kTcM * kTcXs * 4);
+    L.et = o; o = tc_align(o + (size_t)kTcM * kTcXs * 4);
+    L.cols = o; o = tc_align(o + (size_t)(kc + kTcP) * 4);
+    L.end = o;
+    return L;
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) dir_tc_kernel(const DirParams P) {
+    using namespace tc;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    DirTcCtrl &C = *reinterpret_cast<DirTcCtrl *>(smem);
+    const int KC = P.tc_kc;
+    const TcLayout L = tc_layout(KC, P.tc_nmax);
+    float *Ahi = reinterpret_cast<float *>(smem + L.ahi);
+    float *Alo = reinterpret_cast<float *>(smem + L.alo);
+    float *Bhi = reinterpret_cast<float *>(smem + L.bhi);
+    float *Blo = reinterpret_cast<float *>(smem + L.blo);
+    float *Qa = reinterpret_cast<float *>(smem + L.qa);
+    float *Wa = reinterpret_cast<float *>(smem + L.wa);
+    float *XI = reinterpret_cast<float *>(smem + L.xi);
+    float *ET = reinterpret_cast<float *>(smem + L.et);
+    int *colm = reinterpret_cast<int *>(smem + L.cols);   // [KC] column modes, then [16] row modes
+    int *rowm = colm + KC;
+
+    const DirGroup Gp = P.groups[blockIdx.x];
+    const InstDesc d = P.inst[Gp.inst];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long TM = P.total_modes;
+    const int bcl = Gp.a ^ Gp.c;
+    const int nr = pick4d(d.ncls, Gp.a), nc = pick4d(d.ncls, bcl);
+    const int orow = pick4d(d.ocls, Gp.a), ocol = pick4d(d.ocls, bcl);
+    const int nb4 = (nc + 3) & ~3;
+    const int Kp = (nc + 7) & ~7;
+    const int nkch = (Kp + KC - 1) / KC;
+    const int steps = P.steps;
+    const int quarter = warp & 3, half = warp >> 2;
+    const int nloc = quarter * 32 + lane;                  // this thread's step in a tile
+    const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
+    const uint32_t sbo = (uint32_t)(KC / 4) * 128u;
+
+    if (tid == 0) {
+        bar_init(&C.mma_bar, 1);
+        C.fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
+                         su32(&C.tmem))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = C.tmem;
+    uint32_t phase = 0;
+    bool issued = false;
+    bool failed = false;
+
+    for (int kb = 0; kb < Gp.nk && !failed; kb += kTcQ) {
+        const int nq = min(kTcQ, Gp.nk - kb);
+        const int nrow = nq * kTcP;                          // B rows (a multiple of 16)
+        if (tid < nq) {
+            const DirUnit u = P.units[Gp.unit0 + kb + tid];
+            long long sb = 0;
+            for (int a2 = 0; a2 < Gp.a; ++a2) {
+                const int nb2 = (pick4d(d.ncls, a2 ^ Gp.c) + 3) & ~3;
+                sb += (long long)pick4d(d.ncls, a2) * u.mc * nb2;
+            }
+            C.boff[tid] = u.off + sb + (long long)u.kpos * nb4;
+            C.rstride[tid] = u.mc * nb4;
+            C.kk[tid] = (int)(d.k_off + u.kl);
+        }
+        float tot[kTcQ / 2];
+#pragma unroll
+        for (int j = 0; j < kTcQ / 2; ++j) tot[j] = 0.f;
+        __syncthreads();
+        for (int p0 = 0; p0 < nr && !failed; p0 += kTcP) {
+            const int np = min(kTcP, nr - p0);
+            if (tid < kTcP) rowm[tid] = tid < np ? P.perm[d.perm_off + orow + p0 + tid] : 0;
+            for (int t0 = 0; t0 < steps && !failed; t0 += kTcM) {
+                __syncthreads();   // rowm visible; the previous epilogue is done with Qa / XI
+                // q_a, w_a of the chunk's rows and xi, eta of its stress modes for the tile
+                for (int e = tid; e < kTcM * kTcP; e += kTcThreads) {
+                    const int n = e / kTcP, pp = e % kTcP;
+                    float qv = 0.f, wv = 0.f;
+                    if (pp < np && t0 + n < steps) {
+                        const long long g = (long long)(t0 + n) * TM + d.mode_off + rowm[pp];
+                        qv = P.seg_q[g];
+                        wv = P.seg_w[g];
+                    }
+                    Qa[pp * kTcRs + n] = qv;
+                    Wa[pp * kTcRs + n] = wv;
+                }
+                for (int e = tid; e < kTcM * kTcQ; e += kTcThreads) {
+                    const int n = e / kTcQ, q = e % kTcQ;
+                    float xv = 0.f, ev = 0.f;
+                    if (q < nq && t0 + n < steps) {
+                        const long long base = (long long)(t0 + n) * 2 * P.total_k + C.kk[q];
+                        xv = P.xe[base];
+                        ev = P.xe[base + P.total_k];
+                    }
+                    XI[n * kTcXs + q] = xv;
+                    ET[n * kTcXs + q] = ev;
+                }
+                for (int kc = 0; kc < nkch && !failed; ++kc) {
+                    const int k0 = kc * KC;
+                    const int kw = min(KC, Kp - k0);            // multiple of 8
+                    if (tid < KC) colm[tid] = (k0 + tid < nc) ? P.perm[d.perm_off + ocol + k0 + tid] : 0;
+                    __syncthreads();
+                    // A = q_b^T of the tile: element e of the core-matrix image is
+                    // (row n, column s) with e = cm_index(n, s, KC)
+                    for (int e = tid; e < kTcM * KC; e += kTcThreads) {
+                        const int cmi = e >> 5, r = (e >> 2) & 7, cc = e & 3;
+                        const int n = (cmi / (KC >> 2)) * 8 + r;
+                        const int sl = (cmi % (KC >> 2)) * 4 + cc;
+                        float v = 0.f;
+                        if (t0 + n < steps && k0 + sl < nc)
+                            v = P.seg_q[(long long)(t0 + n) * TM + d.mode_off + colm[sl]];
+                        const float h = tf32_hi(v);
+                        Ahi[e] = h;
+                        Alo[e] = v - h;
+                    }
+                    // B = dH rows (k, p) of the chunk, 16-byte pieces
+                    const bool stage_b = (nkch > 1) || (t0 == 0);
+                    if (stage_b) {
+                        for (int e4 = tid; e4 < nrow * (KC >> 2); e4 += kTcThreads) {
+                            const int cmi = e4 >> 3, r = e4 & 7;
+                            const int row = (cmi / (KC >> 2)) * 8 + r;
+                            const int s4 = (cmi % (KC >> 2)) * 4;
+                            const int q = row / kTcP, pp = row % kTcP;
+                            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                            if (pp < np && k0 + s4 < nb4) {
+                                v = __ldg(reinterpret_cast<const float4 *>(
+                                    P.dH + C.boff[q] + (long long)(p0 + pp) * C.rstride[q] + k0 + s4));
+                                if (k0 + s4 + 1 >= nc) v.y = 0.f;
+                                if (k0 + s4 + 2 >= nc) v.z = 0.f;
+                                if (k0 + s4 + 3 >= nc) v.w = 0.f;
+                            }
+                            float4 h, l;
+                            h.x = tf32_hi(v.x);
+                            h.y = tf32_hi(v.y);
+                            h.z = tf32_hi(v.z);
+                            h.w = tf32_hi(v.w);
+                            l.x = v.x - h.x;
+                            l.y = v.y - h.y;
+                            l.z = v.z - h.z;
+                            l.w = v.w - h.w;
+                            reinterpret_cast<float4 *>(Bhi)[e4] = h;
+                            reinterpret_cast<float4 *>(Blo)[e4] = l;
+                        }
+                    }
+                    fence_async_smem();
+                    tc_fence_before();
+                    __syncthreads();
+                    if (tid == 0) {
+                        tc_fence_after();
+                        const uint32_t idesc = idesc_tf32(kTcM, nrow);
+                        const uint32_t ah = su32(Ahi), al = su32(Alo), bh = su32(Bhi), bl = su32(Blo);
+                        for (int ks = 0; ks < kw / 8; ++ks) {
+                            const uint32_t o = (uint32_t)ks * 256u;
+                            const uint64_t ad = smem_desc(ah + o, 128u, sbo);
+                            const uint64_t ald = smem_desc(al + o, 128u, sbo);
+                            const uint64_t bd = smem_desc(bh + o, 128u, sbo);
+                            const uint64_t bld = smem_desc(bl + o, 128u, sbo);
+                            mma_tf32(tmem, ad, bd, idesc, (kc | ks) ? 1u : 0u);
+                            mma_tf32(tmem, ad, bld, idesc, 1u);
+                            mma_tf32(tmem, ald, bd, idesc, 1u);
+                        }
+                        mma_commit(&C.mma_bar);
+                        issued = true;
+                        long long i = 0;
+                        while (!bar_try(&C.mma_bar, phase) && ++i < kTcWait) {
+                        }
+                        if (i >= kTcWait) C.fail = 1;
+                    }
+                    phase ^= 1u;
+                    __syncthreads();
+                    tc_fence_after();
+                    failed = C.fail != 0;
+                }
+                if (failed) break;
+                // epilogue: this thread's step, stress modes q = 2 j + half
+                float qa[kTcP], wa[kTcP];
+#pragma unroll
+                for (int pp = 0; pp < kTcP; ++pp) {
+                    qa[pp] = Qa[pp * kTcRs + nloc];
+                    wa[pp] = Wa[pp * kTcRs + nloc];
+                }
+#pragma unroll
+                for (int j = 0; j < kTcQ / 2; ++j) {
+                    const int q = 2 * j + half;
+                    if (q >= nq) break;
+                    float v[16];
+                    tmem_ld16(tmem + lane_base + (uint32_t)(q * kTcP), v);
+                    float al = 0.f, be = 0.f;
+#pragma unroll
+                    for (int pp = 0; pp < kTcP; ++pp) {
+                        al = fmaf(v[pp], qa[pp], al);
+                        be = fmaf(v[pp], wa[pp], be);
+                    }
+                    tot[j] = fmaf(XI[nloc * kTcXs + q], al, fmaf(ET[nloc * kTcXs + q], be, tot[j]));
+                }
+                tc_fence_before();
+            }
+        }
+        // per stress mode: sum over the 128 steps of a tile (lanes, then the
+        // four warps of a half), then -kappa_k times it into the accumulator
+#pragma unroll
+        for (int j = 0; j < kTcQ / 2; ++j) {
+            const float v = warp_sum(tot[j]);
+            if (lane == 0) C.red[warp][j] = v;
+        }
+        __syncthreads();
+        if (!failed && tid < nq) {
+            const int hh = tid & 1, j = tid >> 1;
+            float t = 0.f;
+            for (int w = 0; w < 4; ++w) t += C.red[hh * 4 + w][j];
+            const int kk = C.kk[tid];
+            P.dir_acc[(long long)kk * 4 + Gp.a] += -(double)P.kappa[kk] * (double)t;
+        }
+        __syncthreads();
+    }
+    if (failed) {
+        set_status(P.status, Gp.inst, MDX_ERR_TIMEOUT);
+        // the MMAs still in flight finish before the tensor memory is released
+        if (tid == 0 && issued) {
+            long long i = 0;
+            while (!bar_try(&C.mma_bar, phase ^ 1u) && ++i < kTcWait) {
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+}
+
+}  // namespace
+
+size_t dir_tc_smem_bytes(int kc, int nmax) { return tc_layout(kc, nmax).end; }
+
+cudaError_t dir_tc_configure(size_t smem) {
+    return cudaFuncSetAttribute(dir_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+}
+
 cudaError_t launch_dir_contract(const DirParams &p, int n_units, cudaStream_t s) {
+    if (p.groups && p.n_groups > 0 && p.tc_kc > 0) {
+        dir_tc_kernel<<<p.n_groups, kTcThreads, p.tc_smem, s>>>(p);
+        return cudaGetLastError();
+    }
     if (p.groups && p.n_groups > 0) {
         dir_class_kernel<false><<<p.n_groups, kDirThreads, 0, s>>>(p);
         return cudaGetLastError();

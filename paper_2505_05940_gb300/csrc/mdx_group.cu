@@ -52,192 +52,13 @@
 
 #include "../../include/mdx.h"
 #include "mdx_common.cuh"
+#include "mdx_tc.cuh"
 
 namespace mdx {
 
 namespace {
 
-// ------------------------------------------------------------------ PTX helpers
-
-__device__ __forceinline__ uint32_t su32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void bar_init(uint64_t *b, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void bar_arrive(uint64_t *b) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
-}
-
-__device__ __forceinline__ void bar_expect_tx(uint64_t *b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool bar_try(uint64_t *b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(su32(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Non-blocking test of a phase parity (no suspension of the thread).
-__device__ __forceinline__ bool bar_test(uint64_t *b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(su32(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait on a phase parity; false when the limit ran out or the launch
-// is aborting.
-__device__ bool bar_wait(uint64_t *b, uint32_t parity, long long limit, volatile int *abort_flag) {
-    for (long long i = 0; i < limit; ++i) {
-        if (bar_try(b, parity)) return true;
-        if ((i & 1023) == 1023 && *abort_flag) return false;
-    }
-    return false;
-}
-
-// The same wait as a tight poll without suspension, for the ring hand-offs
-// whose latency sets the pipeline's throughput.
-__device__ bool bar_spin(uint64_t *b, uint32_t parity, long long limit, volatile int *abort_flag) {
-    for (long long i = 0; i < 64 * limit; ++i) {
-        if (bar_test(b, parity)) return true;
-        if ((i & 4095) == 4095 && *abort_flag) return false;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *b,
-                                          bool hint, uint64_t pol) {
-    if (hint)
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
-            "[%0], [%1], %2, [%3], %4;" ::"r"(su32(dst)),
-            "l"(src), "r"(bytes), "r"(su32(b)), "l"(pol)
-            : "memory");
-    else
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
-            "[%3];" ::"r"(su32(dst)),
-            "l"(src), "r"(bytes), "r"(su32(b))
-            : "memory");
-}
-
-__device__ __forceinline__ uint64_t keep_policy(float fraction) {
-    uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_last.L2::evict_first.b64 %0, %1;"
-                 : "=l"(pol)
-                 : "f"(fraction));
-    return pol;
-}
-
-// Generic-proxy writes to shared memory become visible to the tensor cores.
-__device__ __forceinline__ void fence_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// Round to the nearest TF32 value (ties away from zero); the result is an
-// FP32 number with a zero low 13-bit mantissa.
-__device__ __forceinline__ float tf32_hi(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-
-// Shared-memory matrix descriptor of a K-major operand without swizzle:
-// 8-row x 16-byte core matrices, `lbo` bytes between core matrices adjacent
-// in K, `sbo` bytes between 8-row groups.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;   // descriptor version of the fifth-generation tensor cores
-    return d;                 // base offset 0, swizzle mode 0 (none)
-}
-
-// Instruction descriptor of kind::tf32: FP32 accumulator, TF32 A and B, both
-// K-major, shape M x N.
-__device__ __forceinline__ uint32_t idesc_tf32(int M, int N) {
-    return (1u << 4)                      // D format: F32
-           | (2u << 7)                    // A format: TF32
-           | (2u << 10)                   // B format: TF32
-           | ((uint32_t)(N >> 3) << 17)   // N / 8
-           | ((uint32_t)(M >> 4) << 24);  // M / 16
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-// The mbarrier completes one arrival once every MMA this thread issued so
-// far has finished.
-__device__ __forceinline__ void mma_commit(uint64_t *b) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b))
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr)
-        : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
-        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
-        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
-        "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
-        "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
-        "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
-        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
-        "r"(__float_as_uint(v[15]))
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_wait_st() {
-    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-}
+using namespace tc;
 
 // Named barrier of the four epilogue warps.
 __device__ __forceinline__ void epi_bar() {
@@ -257,12 +78,6 @@ __device__ __forceinline__ float ldcg(const float *p) {
     return v;
 }
 
-// Offset (floats) of element (row, col) in a K-major core-matrix image of
-// `kcols` columns: [row / 8][col / 4][row % 8][col % 4].
-__device__ __forceinline__ int cm_index(int row, int col, int kcols) {
-    return (((row >> 3) * (kcols >> 2) + (col >> 2)) << 5) + ((row & 7) << 2) + (col & 3);
-}
-
 // Writes q of plate b at class-order position pos into a Q image (global or
 // shared): TF32 high part in class a's image, the FP32 remainder in the image
 // that follows it.
@@ -276,12 +91,6 @@ __device__ __forceinline__ void q_image_put(float *img, const GrpDesc &G, int b,
     const float h = tf32_hi(q);
     img[e] = h;
     img[e + G.Bp * kp] = q - h;
-}
-
-// Proxy fence: global-memory writes seen through the generic proxy become
-// visible to the bulk copies (async proxy) this thread issues next.
-__device__ __forceinline__ void fence_async_global() {
-    asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
 // In-warp reduction of 16 values per lane: on return, lane l (l even) holds

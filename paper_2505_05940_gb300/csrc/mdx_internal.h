@@ -222,6 +222,11 @@ struct DirParams {
     double *dH_out;               // [per plate: M][N][N]
     const long long *dh_off;      // [n_inst] double offset of each plate's block
     const int *kperm;             // internal stress index -> user index (at k_off)
+    // tensor-core contraction (class layout): K columns staged per chunk
+    // (multiple of 8; 0 = CUDA-core kernels), B-operand row capacity, status
+    int tc_kc, tc_nmax;
+    size_t tc_smem;
+    int *status;
 };
 
 struct TensionParams {
@@ -392,6 +397,10 @@ struct GradEpilogue {
 };
 cudaError_t launch_grad_epilogue(const GradEpilogue &g, int max_n, cudaStream_t s);
 cudaError_t launch_dir_contract(const DirParams &p, int n_units, cudaStream_t s);
+// Shared memory of the tensor-core contraction for a K chunk of kc columns and
+// nmax B-operand rows; dir_tc_configure raises the kernel's opt-in limit.
+size_t dir_tc_smem_bytes(int kc, int nmax);
+cudaError_t dir_tc_configure(size_t smem);
 // Adds -kappa_k G_k of one segment into p.dH_out (units / groups over every plate).
 cudaError_t launch_dH_accumulate(const DirParams &p, int n_units, cudaStream_t s);
 // dH_out[k][i][j] = dH_out[k][j][i] = their mean, for every plate.

@@ -122,6 +122,9 @@ struct mdx_plan {
     int n_dir_units = 0;
     DirGroup *d_dir_groups = nullptr;
     int n_dir_groups = 0;
+    // tensor-core contraction: K chunk (0 = CUDA-core kernel), B rows, shared memory
+    int dir_tc_kc = 0, dir_tc_nmax = 0;
+    size_t dir_tc_smem = 0;
     // the same units over every plate, for the full dL/dH output
     DirUnit *d_all_units = nullptr;
     int n_all_units = 0;
@@ -555,14 +558,15 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
         // assignment of explicit pieces.
         const int state_cap = 24 * 1024;   // 96 KB of item state per CTA at most
         // shared-memory block of one item: its state arrays, then its stress
-        // modes' d kappa pairs and kappa, then (owner) its gradient sums
-        // (+ the per-mode coefficients and the class permutation, 8 arrays, and the
-        // owner's gradient sums, when the item caches them: plates up to 512 modes)
-        auto item_cached = [&](const InstDesc &d) { return d.Npad <= 512; };
-        auto item_floats = [&](const InstDesc &d, int nk, bool owner) {
-            const bool c = item_cached(d);
+        // modes' d kappa pairs and kappa (+ the per-mode coefficients and the
+        // class permutation, 8 arrays, and the owner's gradient sums, when the
+        // item caches them: plates up to 512 modes, while the CTA's state fits).
+        // The work split is sized without the caches; each CTA then turns them
+        // on item by item within the state budget.
+        auto item_cachable = [&](const InstDesc &d) { return d.Npad <= 512; };
+        auto item_floats = [&](const InstDesc &d, int nk, bool owner, bool cached) {
             return narr * d.Npad + 3 * ((nk + 3) & ~3) +
-                   (c ? 8 * d.Npad + (owner ? 2 * GA_N * d.Npad : 0) : 0);
+                   (cached ? 8 * d.Npad + (owner ? 2 * GA_N * d.Npad : 0) : 0);
         };
         double total = 0.0;
         long long total_kk = 0;
@@ -680,7 +684,8 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
         if (contiguous_ok) {
             for (int g = 0; g < G && contiguous_ok; ++g) {
                 int need = 0;
-                for (const Piece &q : per[g]) need += item_floats(p->inst[q.inst], q.k1 - q.k0, true);
+                for (const Piece &q : per[g])
+                    need += item_floats(p->inst[q.inst], q.k1 - q.k0, true, false);
                 if (need > state_cap) contiguous_ok = false;
             }
         }
@@ -709,7 +714,7 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
             std::vector<int> sfl(G, 0);
             for (const Piece &pc : pieces) {
                 const InstDesc &d = p->inst[pc.inst];
-                const int need = item_floats(d, pc.k1 - pc.k0, true);
+                const int need = item_floats(d, pc.k1 - pc.k0, true, false);
                 int best = -1;
                 for (int g = 0; g < G; ++g) {
                     bool has = false;
@@ -743,6 +748,8 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
             int soff = 0;
             std::sort(per[g].begin(), per[g].end(),
                       [](const Piece &a, const Piece &b) { return a.inst < b.inst; });
+            int spare = state_cap;
+            for (const Piece &q : per[g]) spare -= item_floats(p->inst[q.inst], q.k1 - q.k0, true, false);
             for (const Piece &q : per[g]) {
                 const InstDesc &d = p->inst[q.inst];
                 PlateItem it{};
@@ -753,8 +760,11 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
                 it.slot = (int)(std::find(cl.begin(), cl.end(), g) - cl.begin());
                 it.owner = (it.slot == 0) ? 1 : 0;
                 it.smem_state = soff;
-                it.cache = item_cached(d) ? 1 : 0;
-                soff += item_floats(d, it.k1 - it.k0, it.owner != 0);
+                const int base = item_floats(d, it.k1 - it.k0, it.owner != 0, false);
+                const int extra = item_floats(d, it.k1 - it.k0, it.owner != 0, true) - base;
+                it.cache = (!(p->debug_flags & 4) && item_cachable(d) && extra <= spare) ? 1 : 0;
+                if (it.cache) spare -= extra;
+                soff += base + (it.cache ? extra : 0);
                 items.push_back(it);
                 p->npad_max = std::max(p->npad_max, d.Npad);
             }
@@ -917,6 +927,29 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
             build_units(true, all_units, all_groups);
             p->n_dir_units = (int)units.size();
             p->n_dir_groups = (int)groups.size();
+            if (!groups.empty() && !(p->debug_flags & 8)) {
+                // tensor-core contraction: B rows for up to 16 stress modes x 16 rows;
+                // the K chunk covers a whole class block when shared memory allows
+                int nk_max = 1, kp_max = 8;
+                for (const auto &g : groups) {
+                    const InstDesc &d = p->inst[g.inst];
+                    nk_max = std::max(nk_max, g.nk);
+                    kp_max = std::max(kp_max, (d.ncls[g.a ^ g.c] + 7) & ~7);
+                }
+                const int nmax = 16 * std::min(16, nk_max);
+                int kc = std::min(kp_max, 128);
+                while (kc > 8 && dir_tc_smem_bytes(kc, nmax) + 1024 > (size_t)smem_optin) kc -= 8;
+                const size_t need = dir_tc_smem_bytes(kc, nmax);
+                if (need + 1024 <= (size_t)smem_optin) {
+                    // at least 80 KB, so that at most two CTAs (256 tensor-memory
+                    // columns each) share an SM
+                    p->dir_tc_smem = std::min<size_t>(std::max<size_t>(need, 80 * 1024),
+                                                      (size_t)smem_optin - 1024);
+                    MDX_CUDA(dir_tc_configure(p->dir_tc_smem), "direction contraction attribute");
+                    p->dir_tc_kc = kc;
+                    p->dir_tc_nmax = nmax;
+                }
+            }
             if ((rc2 = upload(p, &p->d_dir_units, units.data(), units.size()))) return bail(rc2);
             if ((rc2 = upload(p, &p->d_dir_groups, groups.data(), groups.size()))) return bail(rc2);
             p->n_all_units = (int)all_units.size();
@@ -1348,6 +1381,10 @@ extern "C" int mdx_grad(mdx_plan *p, const float *exc, const double *q0, const d
         D.steps = seg_len(sg);
         D.total_modes = p->total_modes;
         D.total_k = p->total_k;
+        D.tc_kc = p->parity ? p->dir_tc_kc : 0;
+        D.tc_nmax = p->dir_tc_nmax;
+        D.tc_smem = p->dir_tc_smem;
+        D.status = status;
         mdx_plan::Rec rec{};
         if (p->profiling) {
             rec.which = 3;

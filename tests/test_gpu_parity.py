@@ -224,6 +224,44 @@ def test_gradients_match_oracle_adjoint(kind):
         assert rel(dHg, ref) <= GTOL, rel(dHg, ref)
 
 
+def test_direction_contraction_on_tensor_cores():
+    """The aspect-direction contraction <dL/dH, dH> on the tensor cores
+    (split-TF32 GEMM over each segment's states) against the oracle adjoint,
+    and against the CUDA-core kernel (debug flag 8), on a 90 x 70 plate whose
+    stress classes hold 14-20 modes and row classes 19-25 modes (several
+    16 x 16 chunks of the GEMM's columns) over segments of 256 steps and a
+    ragged last one.  The other gradients do not depend on the contraction
+    and stay bitwise equal."""
+    steps, K = 700, 256
+    wl = W.tiny_random(41, "plate", 90, 70, steps=steps)
+    wl.instances[0].F0 = 300.0
+    oi = oracle_instance(wl.instances[0], wl.fs, wl.steps)
+    rng = np.random.default_rng(1)
+    ybar = rng.normal(size=steps)
+    fc, kc = classes_of(oi)
+    R = rng.normal(size=oi.H.shape)
+    dH = ((R + R.transpose(0, 2, 1)) * ((fc[:, None] ^ fc[None, :])[None] == kc[:, None, None]))
+    dH = dH.astype(np.float32)
+    d = to_plan(oi, wl.fs)
+    d["dH"] = dH
+    yb = torch.tensor(ybar[None, :], dtype=torch.float32, device="cuda")
+    outs = []
+    for flags in (0, 8):
+        sim = modal.Simulator([d], debug_flags=flags)
+        r = sim.simulate(steps, K=K)
+        g = sim.grad(steps, yb, K, r["ckpt"], want_status=True)
+        torch.cuda.synchronize()
+        assert int(g["status"][0]) == 0
+        outs.append(g)
+    adj = oracle.adjoint(oi, ybar, want_dH=True)
+    ref = float(np.sum(adj["dH"] * dH.astype(np.float64)))
+    tc, cc = float(outs[0]["d_dir"][0]), float(outs[1]["d_dir"][0])
+    assert abs(tc - ref) <= GTOL * abs(ref), (tc, ref)
+    assert abs(tc - cc) <= 1e-5 * abs(cc), (tc, cc)
+    for k in ("d_omega2", "d_gamma", "d_b", "d_c", "d_kappa"):
+        assert torch.equal(outs[0][k], outs[1][k]), k
+
+
 def test_gradients_independent_of_checkpoint_interval():
     steps = 1000
     oi, fs = _grad_case("plate", 33, steps)
@@ -238,12 +276,16 @@ def test_gradients_independent_of_checkpoint_interval():
             assert torch.equal(outs[0][k], o[k]), k
 
 
+@pytest.mark.parametrize("flags", [2, 4])
 @pytest.mark.parametrize("force_split", [0, 3])
-def test_fused_sweep_equals_separate_launches(force_split):
+def test_fused_sweep_equals_separate_launches(force_split, flags):
     """The fused adjoint sweep (reverse of segment s and recompute of segment
     s-1 in one launch) gives bitwise the gradients of separate recompute and
-    reverse launches, on a ragged batch with a partial last segment, a
-    direction tensor, and plates shared by several CTAs."""
+    reverse launches (flags 2), and the plate kernel gives bitwise the same
+    audio and gradients without its per-plate shared-memory caches of
+    coefficients and gradient sums (flags 4, the path of plates too large for
+    them), on a ragged batch with a partial last segment, a direction tensor,
+    and plates shared by several CTAs."""
     fs, steps, K = 44100.0, 1100, 256
     insts = [W.tiny_random(50, "plate", 48, 12, steps=steps).instances[0],
              W.tiny_random(51, "string", 30, steps=steps).instances[0],
@@ -264,14 +306,16 @@ def test_fused_sweep_equals_separate_launches(force_split):
         plans.append(d)
     yb = torch.randn(len(ois), steps, dtype=torch.float32, device="cuda")
     outs = []
-    for flags in (0, 2):
-        sim = modal.Simulator(plans, force_split=force_split, debug_flags=flags)
+    for f in (0, flags):
+        sim = modal.Simulator(plans, force_split=force_split, debug_flags=f)
         r = sim.simulate(steps, K=K)
         g = sim.grad(steps, yb, K, r["ckpt"], want_status=True)
         torch.cuda.synchronize()
         assert (g["status"] == 0).all()
+        g["audio"] = r["audio"]
         outs.append(g)
-    for k in ("d_omega2", "d_gamma", "d_b", "d_c", "d_q0", "d_qm1", "d_tau", "d_kappa", "d_dir"):
+    for k in ("audio", "d_omega2", "d_gamma", "d_b", "d_c", "d_q0", "d_qm1", "d_tau", "d_kappa",
+              "d_dir"):
         assert torch.equal(outs[0][k], outs[1][k]), k
 
 

@@ -166,9 +166,11 @@ def test_features_shape_and_finite():
 def test_proposal_beats_prior_on_held_out_targets():
     """Trained on simulator samples, the proposal's estimates of the held-out
     targets' log-parameters are closer than draws from the prior, and fits
-    started from them end at a lower loss than fits from random draws."""
+    started from them end at a lower loss than fits from random draws.  The
+    samples run in plans of 2 048 draws (about 1 000 plates), more plates than
+    the plate kernel's shared memory can give per-plate caches."""
     torch.manual_seed(0)
-    X, Y, wl, bank = proposal.make_dataset(3072, seed=11, steps=4410, batch=1536,
+    X, Y, wl, bank = proposal.make_dataset(3072, seed=11, steps=4410, batch=2048,
                                            aspect_points=4)
     prop, hist = proposal.train(X, Y, epochs=25, batch=128, lr=2e-3, seed=0)
     assert hist[-1] < 0.5 * hist[0]
