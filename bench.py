@@ -343,6 +343,7 @@ def forward_workload(a):
     value = modes * steps / (ms * 1e-3)
     n, pms, pby = sim.plan.kernel_stats(0)
     gn, gms, gby = sim.plan.kernel_stats(5)
+    cn, cms, _ = sim.plan.kernel_stats(6)
     sim.plan.set_profiling(False)
     peak, peak_kind = load_peaks()
     line = {"metric": "mode-steps/s forward", "value": value, "unit": UNIT, "n_gpus": 1,
@@ -356,6 +357,13 @@ def forward_workload(a):
         line["plate_kernel"] = {"GB/s": ach, "frac_of_hbm": ach / peak,
                                 "peak_source": f"{peak_kind} hbm_gbs",
                                 "share_of_time": pms / (ms * a.steps)}
+    if cn:
+        # a few small plates, coupling rows resident in the registers of one
+        # thread-block cluster per plate: bound by the latency of a step's
+        # dependent chain (matvec, reductions, one cluster barrier), not by bytes
+        line["cluster_kernel"] = {"us_per_step": cms * 1e3 / (cn * steps),
+                                  "share_of_time": cms / (ms * a.steps),
+                                  "bound": "latency (H read once per launch)"}
     if gn:
         # grouped plates: one pass over each group's shared coupling tensor per
         # step; the contraction's algorithmic flops are 2 x (nonzero H entries)

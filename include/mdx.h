@@ -142,7 +142,9 @@ typedef struct mdx_options {
                           kernel's shared memory (the path of plates too large for it;
                           equivalence tests);
                           bit 3: run the direction contraction on the CUDA-core kernel instead
-                          of the tensor cores (equivalence tests); 0 in normal use */
+                          of the tensor cores (equivalence tests);
+                          bit 4: run forward passes on the streaming plate kernel even where
+                          the plates fit cluster-resident (equivalence tests); 0 in normal use */
     int scheme;        /* MDX_SCHEME_SV (default) or MDX_SCHEME_TF */
     int group_engine;  /* plates with geom_group > 0: MDX_GROUP_TF32X3 (default) steps each
                           group with one shared coupling tensor on the tensor cores;
@@ -366,7 +368,10 @@ double mdx_plan_l2_keep(const mdx_plan *plan);
  * contraction of the direction tensor, 4 = fused sweep: the adjoint of one
  * segment and the recompute of the previous one in the same launch,
  * 5 = grouped plates on the tensor cores: bytes are the nonzero class blocks
- * of each group's shared coupling tensor, one pass per step), the
+ * of each group's shared coupling tensor, one pass per step, 6 = forward pass
+ * of a few plates with their coupling rows resident in the registers of one
+ * thread-block cluster per plate: bytes count one pass over H per step as for
+ * class 0, although H is read from memory once per launch), the
  * number of launches, their summed device time in ms and their summed
  * algorithmic bytes (coupling-tensor bytes each launch must stream: one pass
  * over H per step; the direction tensor is counted by class 3).

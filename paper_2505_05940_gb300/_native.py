@@ -341,7 +341,8 @@ class Plan:
 
     def kernel_stats(self, which):
         """which: 0 forward, 1 recompute, 2 reverse, 3 direction contraction,
-        4 fused sweep, 5 grouped plates -> (launches, ms, bytes)."""
+        4 fused sweep, 5 grouped plates, 6 cluster-resident forward
+        -> (launches, ms, bytes)."""
         n = ctypes.c_long()
         ms = ctypes.c_double()
         by = ctypes.c_double()

@@ -1,8 +1,10 @@
 """Tile autotuner for the plate kernel.
 
-For a given set of instances the tuner times a short forward run for each
-candidate TMA stage size (the ring depth follows from the shared memory left
-over) and keeps the fastest.  Results are cached in a JSON file keyed by the
+For a given set of instances the tuner times a short checkpointed forward
+run (the streaming plate kernel, which also serves every gradient pass) for
+each candidate TMA stage size (the ring depth follows from the shared memory
+left over) and keeps the fastest.  Checkpoint-free forward passes of a few
+small plates run cluster-resident instead and have no stages to tune.  Results are cached in a JSON file keyed by the
 GPU name and a signature of the plate shapes, so a workload is tuned once per
 device type.  Timing uses the library's own per-launch CUDA events
 (mdx_plan_kernel_stats).
@@ -60,12 +62,12 @@ def tune(sim, steps=128, repeats=2, cache_path=None, candidates=STAGE_CANDIDATES
         except Exception as e:  # does not fit in shared memory
             trials.append({"stage_bytes": stage, "error": str(e)})
             continue
-        sim.simulate(steps)
+        sim.simulate(steps, K=steps)
         torch.cuda.synchronize()
         sim.plan.set_profiling(True)
         sim.plan.reset_stats()
         for _ in range(repeats):
-            sim.simulate(steps)
+            sim.simulate(steps, K=steps)
         n, ms, _ = sim.plan.kernel_stats(0)
         sim.plan.set_profiling(False)
         trials.append({"stage_bytes": stage, "us_per_step": 1e3 * ms / max(n, 1) / steps,

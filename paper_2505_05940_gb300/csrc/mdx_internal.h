@@ -229,6 +229,40 @@ struct DirParams {
     int *status;
 };
 
+// Cluster-resident plates: one thread-block cluster per plate, the plate's
+// coupling rows held in registers for the whole launch (forward pass).
+struct ClusterK {
+    long long off;     // float offset of the stress mode's class chunk (H)
+    int mc, kpos, c;   // chunk size, position in the chunk, class
+    int pad;
+};
+
+struct ClusterParams {
+    const InstDesc *inst;
+    const int *plates;            // plate instance indices (one cluster each)
+    const ClusterK *kinfo;        // [total_k]
+    const float *H;
+    const float *kappa;
+    const int *perm;
+    ModeCoef coef;
+    int cs;                       // CTAs per cluster
+    int nkc;                      // stress-mode slots per CTA
+    int wk;                       // warps per slot (rows: class-ordered modes)
+    int steps, n_begin, total_steps;
+    const float *exc;
+    float *audio;
+    float *state_io;              // [4][total_modes]: q_hi, q_lo, v_hi, v_lo
+    long long total_modes;
+    int *status;
+};
+
+// Row length (floats) of the register-resident coupling rows: 32 or 64; 0
+// when a plate does not fit.  cluster_plan picks the cluster shape.
+int cluster_row_len(int max_class);
+int cluster_max_threads(int row_len);
+cudaError_t launch_cluster(const ClusterParams &P, int n_plates, int row_len, cudaStream_t s);
+cudaError_t cluster_check(int cs, int threads, int row_len, int *max_clusters);
+
 struct TensionParams {
     const InstDesc *inst;
     const int *list;              // tension instance indices

@@ -103,8 +103,8 @@ struct mdx_plan {
         cudaEvent_t a, b;
     };
     std::vector<Rec> recs;
-    long stat_launch[6] = {0, 0, 0, 0, 0, 0};
-    double stat_ms[6] = {0, 0, 0, 0, 0, 0}, stat_bytes[6] = {0, 0, 0, 0, 0, 0};
+    long stat_launch[7] = {0, 0, 0, 0, 0, 0, 0};
+    double stat_ms[7] = {0, 0, 0, 0, 0, 0, 0}, stat_bytes[7] = {0, 0, 0, 0, 0, 0, 0};
     double H_bytes_per_step = 0, dH_bytes_per_step = 0;
     int smem_optin = 0;
     // L2 residency of the coupling stream: requested fraction (< 0: automatic)
@@ -146,6 +146,11 @@ struct mdx_plan {
     GroupPlan *grp = nullptr;
     std::vector<int> grouped;      // per instance
     bool any_grouped = false;
+    // cluster-resident forward pass (few plates, class layout): one cluster per plate
+    bool cluster_ok = false;
+    int cl_cs = 0, cl_nkc = 0, cl_wk = 0, cl_rl = 0, n_cplates = 0;
+    ClusterK *d_kinfo = nullptr;
+    int *d_cplates = nullptr;
 };
 
 namespace {
@@ -864,6 +869,57 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
             if ((rc2 = upload(p, &p->d_perm, perm_all.data(), perm_all.size()))) return bail(rc2);
             if ((rc2 = upload(p, &p->d_kperm, kperm_all.data(), kperm_all.size()))) return bail(rc2);
             if ((rc2 = upload(p, &p->d_chunks, chunks.data(), chunks.size()))) return bail(rc2);
+            // cluster-resident forward pass: every plate's rows in the registers of
+            // one cluster (class blocks of at most 64 modes, at most 512 threads a
+            // CTA), and all clusters resident at once
+            {
+                std::vector<int> cplates;
+                int maxN = 0, maxM = 0, maxcls = 0;
+                for (int i = 0; i < n_inst; ++i) {
+                    const InstDesc &d = p->inst[i];
+                    if (d.kind != MDX_KIND_PLATE || d.M == 0 || d.grouped) continue;
+                    cplates.push_back(i);
+                    maxN = std::max(maxN, d.N);
+                    maxM = std::max(maxM, d.M);
+                    for (int a = 0; a < 4; ++a) maxcls = std::max(maxcls, d.ncls[a]);
+                }
+                const int rl = cluster_row_len(maxcls);
+                const int wk = (maxN + 31) / 32;
+                if (!cplates.empty() && rl > 0 && !(p->debug_flags & 16)) {
+                    for (int cs : {std::min(maxM, 8), 16}) {
+                        if (cs > maxM && cs != std::min(maxM, 8)) break;
+                        const int nkc = (maxM + cs - 1) / cs;
+                        const int threads = nkc * wk * 32;
+                        if (threads > cluster_max_threads(rl)) continue;
+                        int fit = 0;
+                        if (cluster_check(cs, threads, rl, &fit) != cudaSuccess) {
+                            cudaGetLastError();
+                            continue;
+                        }
+                        if (fit < (int)cplates.size()) continue;
+                        std::vector<ClusterK> kinfo(std::max<long long>(p->total_k, 1));
+                        for (const auto &it : items)
+                            for (int ci = it.chunk0; ci < it.chunk1; ++ci)
+                                for (int q = 0; q < chunks[ci].mc; ++q) {
+                                    ClusterK &K = kinfo[p->inst[it.inst].k_off + chunks[ci].kl0 + q];
+                                    K.off = chunks[ci].off;
+                                    K.mc = chunks[ci].mc;
+                                    K.kpos = q;
+                                    K.c = chunks[ci].c;
+                                }
+                        if ((rc2 = upload(p, &p->d_kinfo, kinfo.data(), kinfo.size()))) return bail(rc2);
+                        if ((rc2 = upload(p, &p->d_cplates, cplates.data(), cplates.size())))
+                            return bail(rc2);
+                        p->cluster_ok = true;
+                        p->cl_cs = cs;
+                        p->cl_nkc = nkc;
+                        p->cl_wk = wk;
+                        p->cl_rl = rl;
+                        p->n_cplates = (int)cplates.size();
+                        break;
+                    }
+                }
+            }
             // contraction units: plates with a direction tensor (direction
             // derivative), and every plate (full dL/dH output)
             auto build_units = [&](bool all, std::vector<DirUnit> &units,
@@ -1148,8 +1204,46 @@ TensionParams base_tension(mdx_plan *p, int mode, int steps, int n_begin, int to
     return T;
 }
 
+int run_cluster(mdx_plan *p, const PlateParams &P, cudaStream_t s) {
+    ClusterParams C{};
+    C.inst = p->d_inst;
+    C.plates = p->d_cplates;
+    C.kinfo = p->d_kinfo;
+    C.H = p->d_H;
+    C.kappa = p->d_kappa;
+    C.perm = p->d_perm;
+    C.coef = p->coef;
+    C.cs = p->cl_cs;
+    C.nkc = p->cl_nkc;
+    C.wk = p->cl_wk;
+    C.steps = P.steps;
+    C.n_begin = P.n_begin;
+    C.total_steps = P.total_steps;
+    C.exc = P.exc;
+    C.audio = P.audio;
+    C.state_io = P.state_io;
+    C.total_modes = p->total_modes;
+    C.status = P.status;
+    mdx_plan::Rec rec{};
+    if (p->profiling) {
+        rec.which = 6;
+        rec.bytes = (double)P.steps * p->H_bytes_per_step;
+        MDX_CUDA(cudaEventCreate(&rec.a), "event");
+        MDX_CUDA(cudaEventCreate(&rec.b), "event");
+        MDX_CUDA(cudaEventRecord(rec.a, s), "event");
+    }
+    MDX_CUDA(launch_cluster(C, p->n_cplates, p->cl_rl, s), "cluster plate kernel");
+    if (p->profiling) {
+        MDX_CUDA(cudaEventRecord(rec.b, s), "event");
+        p->recs.push_back(rec);
+    }
+    return MDX_OK;
+}
+
 int run_plate(mdx_plan *p, PlateParams &P, cudaStream_t s) {
     if (!p->any_plate) return MDX_OK;
+    // a forward pass without checkpoints of a few small plates: cluster-resident
+    if (p->cluster_ok && P.mode == MODE_FORWARD && !P.ckpt) return run_cluster(p, P, s);
     MDX_CUDA(cudaMemsetAsync(p->d_counters, 0, p->n_inst * sizeof(unsigned), s), "memset");
     MDX_CUDA(cudaMemsetAsync(p->d_abort, 0, sizeof(int), s), "memset");
     const size_t smem = (P.mode == MODE_FUSED) ? p->smem_fused
@@ -1669,14 +1763,14 @@ extern "C" int mdx_plan_reset_stats(mdx_plan *p) {
         cudaEventDestroy(r.b);
     }
     p->recs.clear();
-    for (int i = 0; i < 6; ++i) p->stat_launch[i] = 0, p->stat_ms[i] = 0, p->stat_bytes[i] = 0;
+    for (int i = 0; i < 7; ++i) p->stat_launch[i] = 0, p->stat_ms[i] = 0, p->stat_bytes[i] = 0;
     return MDX_OK;
 }
 
 extern "C" int mdx_plan_kernel_stats(mdx_plan *p, int which, long *launches, double *ms,
                                      double *bytes) {
     if (!p) return fail(MDX_ERR_ARG, "plan is NULL");
-    if (which < 0 || which > 5) return fail(MDX_ERR_ARG, "which must be 0..5");
+    if (which < 0 || which > 6) return fail(MDX_ERR_ARG, "which must be 0..6");
     for (auto &r : p->recs) {
         MDX_CUDA(cudaEventSynchronize(r.b), "event sync");
         float t = 0.f;

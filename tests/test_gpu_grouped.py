@@ -94,7 +94,10 @@ def test_grouped_small_group_against_oracle():
     blocks = int(np.sum((fc[:, None] ^ fc[None, :])[None] == kc[:, None, None]))
     assert sim.plan.group_work()[0] == 4 * blocks
     ref_cc, qref_cc, _, csim = _run(plans, steps, group_engine="off")
-    assert csim.plan.kernel_stats(5)[0] == 0 and csim.plan.kernel_stats(0)[0] == 1
+    # per-instance copies: the streaming kernel or, for a few small plates,
+    # the cluster-resident one
+    assert csim.plan.kernel_stats(5)[0] == 0
+    assert csim.plan.kernel_stats(0)[0] + csim.plan.kernel_stats(6)[0] == 1
     for i, oi in enumerate(ois):
         ref = oracle.forward(oi, steps=steps)
         ea, eq = rel(audio[i], ref["y"]), rel(qend[i], ref["qN"])

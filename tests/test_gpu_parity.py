@@ -63,8 +63,10 @@ def to_plan(oi, fs, layout="classes"):
     return d
 
 
-def run_gpu(ois, fs, steps, layout="classes", **opts):
+def run_gpu(ois, fs, steps, layout="classes", force_profile=False, **opts):
     sim = modal.Simulator([to_plan(o, fs, layout) for o in ois], **opts)
+    if force_profile:
+        sim.plan.set_profiling(True)
     r = sim.simulate(steps, want_state=True, want_status=True)
     torch.cuda.synchronize()
     off = sim.plan.mode_offset
@@ -260,6 +262,39 @@ def test_direction_contraction_on_tensor_cores():
     assert abs(tc - cc) <= 1e-5 * abs(cc), (tc, cc)
     for k in ("d_omega2", "d_gamma", "d_b", "d_c", "d_kappa"):
         assert torch.equal(outs[0][k], outs[1][k]), k
+
+
+def test_cluster_resident_forward_matches_oracle_and_streaming_kernel():
+    """A checkpoint-free forward pass of a few small plates runs with each
+    plate's coupling rows in the registers of one thread-block cluster (stats
+    class 6).  A 100 x 30 plate, a 48 x 12 and a 20 x 4 plate (one shape for
+    all: clusters of 8 CTAs with 4 stress-mode slots each, so the small plates
+    leave slots and CTAs empty) and a string in one plan, against the oracle
+    and against the streaming kernel (debug flag 16), over 3 000 steps
+    (excitation staged in blocks of 256 steps)."""
+    fs, steps = 44100.0, 3000
+    insts = [W.tiny_random(60, "plate", 100, 30, steps=steps).instances[0],
+             W.tiny_random(61, "plate", 48, 12, steps=steps).instances[0],
+             W.tiny_random(62, "plate", 20, 4, steps=steps).instances[0],
+             W.tiny_random(63, "string", 30, steps=steps).instances[0]]
+    for x in insts[:3]:
+        x.F0 = 300.0
+    ois = [oracle_instance(i, fs, steps) for i in insts]
+    outs = []
+    for flags in (0, 16):
+        audio, qend, status, sim = run_gpu(ois, fs, steps, debug_flags=flags, force_profile=True)
+        assert (status == 0).all(), status
+        outs.append((audio, qend))
+        if flags == 0:
+            assert sim.plan.kernel_stats(6)[0] == 1 and sim.plan.kernel_stats(0)[0] == 0
+        else:
+            assert sim.plan.kernel_stats(6)[0] == 0 and sim.plan.kernel_stats(0)[0] == 1
+    for i, oi in enumerate(ois):
+        ref = oracle.forward(oi, steps=steps)
+        for audio, qend in outs:
+            assert rel(audio[i], ref["y"]) <= TOL, (i, rel(audio[i], ref["y"]))
+            assert rel(qend[i], ref["qN"]) <= TOL, (i, rel(qend[i], ref["qN"]))
+        assert rel(outs[0][0][i], outs[1][0][i]) <= 5e-6
 
 
 def test_gradients_independent_of_checkpoint_interval():
