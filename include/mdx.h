@@ -541,6 +541,26 @@ int mdx_adam_step(long long n, float *w, uint16_t *w_bf16, const float *g, float
 int mdx_f32_to_bf16(long long n, const float *x, uint16_t *y, void *stream);
 
 /*
+ * Log-mel features of a batch of signals: the input of the learned proposal
+ * network (the paper has no network or feature front end; its fits start
+ * from random draws, Sec. 4.3).  For each signal x (length T) and segment s:
+ * the power spectra of centred frames (the signal extended by reflection by
+ * n_fft / 2 on both sides, hop `hop`, periodic Hann window), projected on
+ * n_mels triangular filters equally spaced on the HTK mel scale
+ * mel(f) = 2595 log10(1 + f / 700) between fmin and fmax, log(. + 1e-6),
+ * averaged over the frames floor(s F / S) .. floor((s + 1) F / S) - 1 (at least
+ * one), F = 1 + T / hop frames, S = segments.
+ *   audio  device [batch][T] FP32
+ *   out    device [batch][n_mels][segments] FP32 (overwritten)
+ * Deterministic (fixed summation order).  Allocates nothing.
+ * Errors: MDX_ERR_ARG (n_fft not a power of two in [16, 2048], T <= n_fft / 2,
+ * fewer frames than segments, n_mels outside [1, 512], frequencies outside
+ * 0 <= fmin < fmax <= fs / 2, NULL buffers), MDX_ERR_CUDA (launch).
+ */
+int mdx_logmel(const float *audio, int batch, int T, double fs, int n_fft, int hop, int n_mels,
+               double fmin, double fmax, int segments, float *out, void *stream);
+
+/*
  * Forward run of strings and membranes that allocates no device memory.
  * The paper has no counterpart: this entry point exists for callers that must
  * not call cudaMalloc, such as a real-time audio callback (cudaMalloc can

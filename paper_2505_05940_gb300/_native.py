@@ -31,7 +31,7 @@ EXPORTED = ("mdx_last_error", "mdx_version", "mdx_plan_create", "mdx_plan_destro
             "mdx_adam_step", "mdx_f32_to_bf16", "mdx_plan_set_l2_keep", "mdx_plan_l2_keep",
             "mdx_difference_coefficients", "mdx_coefficient_grads", "mdx_modal_from_physics",
             "mdx_physics_vjp", "mdx_plan_group_work", "mdx_plan_set_coupling",
-            "mdx_linear_workspace_bytes", "mdx_simulate_linear")
+            "mdx_linear_workspace_bytes", "mdx_simulate_linear", "mdx_logmel")
 
 
 class MdxError(RuntimeError):
@@ -159,6 +159,8 @@ def load(build_if_missing: bool = True):
         L.mdx_adam_step.argtypes = [ctypes.c_longlong, vp, vp, vp, vp, vp, ctypes.c_float,
                                     ctypes.c_float, ctypes.c_float, ctypes.c_float, i32, vp]
         L.mdx_f32_to_bf16.argtypes = [ctypes.c_longlong, vp, vp, vp]
+        L.mdx_logmel.argtypes = [vp, i32, i32, ctypes.c_double, i32, i32, i32, ctypes.c_double,
+                                 ctypes.c_double, i32, vp, vp]
         L.mdx_plan_configure.argtypes = [vp, i32, i32]
         L.mdx_plan_set_l2_keep.argtypes = [vp, ctypes.c_double]
         L.mdx_plan_l2_keep.argtypes = [vp]
@@ -497,3 +499,19 @@ def physics_vjp(ph, n_phi, n_psi, d_omega2, d_gamma, d_tau=0.0, d_kappa=None, d_
                                  dz.ctypes.data_as(_D) if dz is not None else None,
                                  ctypes.byref(out)))
     return {k: getattr(out, k) for k, _ in PhysicsGrads._fields_}
+
+
+def logmel(audio, fs=44100.0, n_fft=1024, hop=256, n_mels=128, fmin=20.0, fmax=None,
+           segments=8, stream=None):
+    """mdx_logmel: [B, T] FP32 CUDA tensor -> [B, n_mels * segments] log-mel
+    features (mel-major, segments innermost)."""
+    import torch
+    if not (audio.is_cuda and audio.dtype == torch.float32 and audio.dim() == 2):
+        raise ValueError("audio must be a [batch, T] float32 CUDA tensor")
+    x = audio.contiguous()
+    B, T = x.shape
+    out = torch.empty(B, n_mels * segments, dtype=torch.float32, device=x.device)
+    check(load().mdx_logmel(_ptr(x), B, T, float(fs), n_fft, hop, n_mels, float(fmin),
+                            float(fs / 2.0 if fmax is None else fmax), segments, _ptr(out),
+                            _stream(stream)))
+    return out

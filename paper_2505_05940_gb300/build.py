@@ -19,7 +19,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libmdx.so")
 SOURCES = ["mdx_plan.cu", "mdx_tension.cu", "mdx_plate.cu", "mdx_aux.cu", "mdx_noalloc.cu",
            "mdx_dir.cu", "mdx_mlp.cu", "mdx_physics.cu", "mdx_group.cu",
-           "mdx_linear.cu", "mdx_cluster.cu"]
+           "mdx_linear.cu", "mdx_cluster.cu", "mdx_features.cu"]
 HEADERS = ["mdx_internal.h", "mdx_common.cuh", "mdx_scheme.cuh", "mdx_tc.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

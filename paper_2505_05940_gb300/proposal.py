@@ -45,33 +45,13 @@ def log_params(inst):
 
 # ----------------------------------------------------------------- features
 
-def mel_filterbank(n_fft, fs, n_mels=128, fmin=20.0, fmax=None, device="cpu"):
-    """Triangular filters equally spaced on the mel scale (HTK formula)."""
-    fmax = fmax or fs / 2.0
-    mel = lambda f: 2595.0 * np.log10(1.0 + f / 700.0)
-    imel = lambda m: 700.0 * (10.0 ** (m / 2595.0) - 1.0)
-    pts = imel(np.linspace(mel(fmin), mel(fmax), n_mels + 2))
-    freqs = np.linspace(0.0, fs / 2.0, n_fft // 2 + 1)
-    fb = np.zeros((n_mels, len(freqs)))
-    for i in range(n_mels):
-        lo, c, hi = pts[i], pts[i + 1], pts[i + 2]
-        up = (freqs - lo) / max(c - lo, 1e-9)
-        dn = (hi - freqs) / max(hi - c, 1e-9)
-        fb[i] = np.maximum(0.0, np.minimum(up, dn))
-    return torch.tensor(fb, dtype=torch.float32, device=device)
-
-
 def features(audio, fs=44100.0, n_fft=1024, hop=256, n_mels=128, segments=8):
-    """audio [B, T] (GPU) -> [B, n_mels * segments] log-mel features."""
-    win = torch.hann_window(n_fft, device=audio.device)
-    X = torch.stft(audio, n_fft=n_fft, hop_length=hop, window=win, center=True,
-                   return_complex=True).abs() ** 2                       # [B, F, frames]
-    fb = mel_filterbank(n_fft, fs, n_mels, device=audio.device)
-    m = torch.log(torch.einsum("mf,bft->bmt", fb, X) + 1e-6)            # [B, mels, frames]
-    frames = m.shape[-1]
-    edges = np.linspace(0, frames, segments + 1).astype(int)
-    pooled = [m[..., edges[i]:max(edges[i + 1], edges[i] + 1)].mean(-1) for i in range(segments)]
-    return torch.stack(pooled, -1).reshape(audio.shape[0], -1)
+    """audio [B, T] (GPU) -> [B, n_mels * segments] log-mel features (the
+    library's mdx_logmel kernel: power STFT with a periodic Hann window and
+    centred frames, HTK-mel triangles from 20 Hz to fs / 2, log(. + 1e-6),
+    mean over `segments` equal frame ranges)."""
+    return _native.logmel(audio, fs=fs, n_fft=n_fft, hop=hop, n_mels=n_mels, fmin=20.0,
+                          segments=segments)
 
 
 # ----------------------------------------------------------------- network

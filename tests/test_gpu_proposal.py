@@ -16,6 +16,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 import oracle
 from oracle import mlp_oracle as MO
 from oracle import physics_oracle as PO
+from paper_2505_05940_gb300 import _native as N
 from paper_2505_05940_gb300 import modal, proposal, workloads as W
 
 from test_gpu_parity import TOL, oracle_instance, rel, to_plan
@@ -161,6 +162,63 @@ def test_features_shape_and_finite():
     audio = torch.randn(3, 11025, device="cuda:0") * 1e-3
     f = proposal.features(audio)
     assert f.shape == (3, 1024) and torch.isfinite(f).all()
+    silent = proposal.features(torch.zeros(2, 11025, device="cuda:0"))
+    assert torch.allclose(silent, torch.full_like(silent, float(np.log(np.float32(1e-6)))))
+
+
+def _logmel_ref(x, fs, n_fft, hop, n_mels, fmin, fmax, S):
+    """The features from their definition in FP64 numpy: reflection-padded
+    centred frames, periodic Hann window, |rfft|^2, HTK-mel triangles,
+    log(. + 1e-6), mean over frames floor(s F / S) .. floor((s+1) F / S) - 1."""
+    xp = np.pad(np.asarray(x, np.float64), (n_fft // 2, n_fft // 2), mode="reflect")
+    F = 1 + len(x) // hop
+    w = 0.5 * (1.0 - np.cos(2.0 * np.pi * np.arange(n_fft) / n_fft))
+    P = np.stack([np.abs(np.fft.rfft(xp[f * hop:f * hop + n_fft] * w)) ** 2 for f in range(F)], 1)
+    mel = lambda f: 2595.0 * np.log10(1.0 + f / 700.0)
+    imel = lambda m: 700.0 * (10.0 ** (m / 2595.0) - 1.0)
+    pts = imel(np.linspace(mel(fmin), mel(fmax), n_mels + 2))
+    freqs = np.linspace(0.0, fs / 2, n_fft // 2 + 1)
+    fb = np.array([np.clip(np.minimum((freqs - pts[i]) / (pts[i + 1] - pts[i]),
+                                      (pts[i + 2] - freqs) / (pts[i + 2] - pts[i + 1])), 0, None)
+                   for i in range(n_mels)])
+    m = np.log(fb @ P + 1e-6)
+    out = np.empty((n_mels, S))
+    for s in range(S):
+        a, b = (s * F) // S, ((s + 1) * F) // S
+        out[:, s] = m[:, a:max(b, a + 1)].mean(1)
+    return out.reshape(-1)
+
+
+@pytest.mark.parametrize("cfg", [(1024, 256, 128, 20.0, None, 8, 11025),
+                                 (512, 100, 40, 50.0, 8000.0, 5, 4410),
+                                 (2048, 512, 64, 0.0, None, 3, 9000)])
+def test_features_kernel_matches_definition(cfg):
+    """mdx_logmel against the FP64 definition on decaying partials (the shape
+    of the simulator's output) and on noise; at the proposal's configuration
+    the frames are also pinned to the spectral-loss oracle's STFT."""
+    n_fft, hop, n_mels, fmin, fmax, S, T = cfg
+    fs = 44100.0
+    fmax = fmax or fs / 2
+    rng = np.random.default_rng(n_fft + hop)
+    t = np.arange(T) / fs
+    sigs = [sum(a * np.exp(-t * d) * np.sin(2 * np.pi * f0 * t + ph)
+                for a, d, f0, ph in zip(rng.uniform(1e-4, 1e-2, 6), rng.uniform(1, 30, 6),
+                                        rng.uniform(60, 8000, 6), rng.uniform(0, 6.28, 6))),
+            rng.standard_normal(T) * 1e-3]
+    x = np.stack(sigs).astype(np.float32)
+    got = N.logmel(torch.tensor(x, device="cuda"), fs=fs, n_fft=n_fft, hop=hop, n_mels=n_mels,
+                   fmin=fmin, fmax=fmax, segments=S).cpu().numpy()
+    for i in range(len(x)):
+        ref = _logmel_ref(x[i].astype(np.float64), fs, n_fft, hop, n_mels, fmin, fmax, S)
+        np.testing.assert_allclose(got[i], ref, rtol=2e-4, atol=2e-4)
+    if cfg[0] == 1024:
+        from oracle import stft_oracle as SO
+        P = SO.stft_mag(x[0].astype(np.float64), 1024) ** 2
+        assert P.shape[1] == 1 + T // 256
+        ref_frames = np.abs(np.fft.rfft(np.pad(x[0].astype(np.float64), (512, 512), mode="reflect")[
+            256 * 7:256 * 7 + 1024] * 0.5 * (1 - np.cos(2 * np.pi * np.arange(1024) / 1024)))) ** 2
+        np.testing.assert_allclose(P[:, 7], ref_frames, rtol=1e-12)
+        assert np.allclose(proposal.features(torch.tensor(x, device="cuda")).cpu().numpy(), got)
 
 
 def test_proposal_beats_prior_on_held_out_targets():

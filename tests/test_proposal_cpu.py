@@ -1,5 +1,6 @@
 """Host-side logic of the learned proposal (no GPU): parametrisation, the
-stability projection, mel filters and the study's bookkeeping."""
+stability projection, the feature kernel's argument checks and the study's
+bookkeeping."""
 import numpy as np
 import pytest
 
@@ -50,26 +51,26 @@ def test_projection_keeps_scheme_stable_and_ratio():
     np.testing.assert_array_equal(proposal._project(preps, lp.copy(), 1.0 / wl.fs), lp)
 
 
-def test_mel_filterbank_centres_and_peaks():
-    fs, n_fft = 44100.0, 1024
-    fb = proposal.mel_filterbank(n_fft, fs, 128).numpy()
-    assert fb.shape == (128, n_fft // 2 + 1)
-    assert np.all(fb >= 0) and np.all(fb.max(1) <= 1 + 1e-6)
-    freqs = np.linspace(0, fs / 2, n_fft // 2 + 1)
-    centres = freqs[np.argmax(fb, 1)]
-    mel = 2595.0 * np.log10(1.0 + centres / 700.0)
-    # centres are monotone and evenly spaced on the mel scale (to a bin's width)
-    assert np.all(np.diff(centres) >= 0)
-    step = (2595.0 * np.log10(1 + (fs / 2) / 700.0) - 2595.0 * np.log10(1 + 20 / 700.0)) / 129
-    high = mel[64:]
-    assert np.allclose(np.diff(high), step, atol=step * 0.5)
+def test_logmel_rejects_invalid_arguments():
+    """mdx_logmel validates its arguments before any device work (no GPU
+    needed): NULL buffers, n_fft not a power of two or out of range, a signal
+    too short for the reflection padding, fewer frames than segments, a mel
+    count outside [1, 512], frequencies outside 0 <= fmin < fmax <= fs / 2."""
+    import ctypes
+    from paper_2505_05940_gb300 import _native as N
+    L = N.load()
+    fake = ctypes.c_void_p(16)   # never dereferenced: every call fails validation
 
+    def call(audio=fake, B=1, T=11025, fs=44100.0, n_fft=1024, hop=256, mels=128, fmin=20.0,
+             fmax=22050.0, seg=8, out=fake):
+        return L.mdx_logmel(audio, B, T, fs, n_fft, hop, mels, fmin, fmax, seg, out, None)
 
-def test_features_cpu_shape():
-    audio = torch.zeros(2, 11025)
-    audio[:, 100] = 1.0
-    f = proposal.features(audio)
-    assert f.shape == (2, 1024) and torch.isfinite(f).all()
+    for kw in (dict(audio=None), dict(out=None), dict(B=0), dict(seg=0), dict(n_fft=1000),
+               dict(n_fft=8), dict(n_fft=4096), dict(hop=0), dict(T=512), dict(T=600, seg=8),
+               dict(mels=0), dict(mels=513), dict(fmin=-1.0), dict(fmax=20.0),
+               dict(fmax=30000.0), dict(fs=0.0)):
+        assert call(**kw) == 1, kw
+        assert L.mdx_last_error()
 
 
 def test_summarize_counts_unreached():
@@ -87,25 +88,3 @@ def test_random_init_keeps_kind_and_aspect():
         assert lp[2] == pytest.approx(proposal.log_params(t)[2])
 
 
-def test_features_match_numpy_definition():
-    """Log-mel features (power STFT with a periodic Hann window, hop 256,
-    centred frames; HTK-mel triangles; log(mel + 1e-6); mean over 8 equal
-    frame segments) recomputed with numpy from the definition."""
-    from oracle import stft_oracle as SO
-    rng = np.random.default_rng(5)
-    x = (rng.standard_normal(11025) * 1e-2).astype(np.float32)
-    got = proposal.features(torch.tensor(x[None]), fs=44100.0)[0].numpy()
-    n_fft, fs = 1024, 44100.0
-    # the STFT oracle's frames use hop n_fft / 4 = 256, as the features do
-    P = SO.stft_mag(x.astype(np.float64), n_fft) ** 2
-    mel = lambda f: 2595.0 * np.log10(1.0 + f / 700.0)
-    imel = lambda m: 700.0 * (10.0 ** (m / 2595.0) - 1.0)
-    pts = imel(np.linspace(mel(20.0), mel(fs / 2), 130))
-    freqs = np.linspace(0.0, fs / 2, n_fft // 2 + 1)
-    fb = np.array([np.clip(np.minimum((freqs - pts[i]) / (pts[i + 1] - pts[i]),
-                                      (pts[i + 2] - freqs) / (pts[i + 2] - pts[i + 1])), 0, None)
-                   for i in range(128)])
-    m = np.log(fb @ P + 1e-6)
-    edges = np.linspace(0, m.shape[1], 9).astype(int)
-    ref = np.stack([m[:, edges[i]:max(edges[i + 1], edges[i] + 1)].mean(1) for i in range(8)], 1)
-    np.testing.assert_allclose(got, ref.reshape(-1), rtol=2e-4, atol=2e-4)
