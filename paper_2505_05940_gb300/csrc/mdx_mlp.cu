@@ -2,26 +2,38 @@
 //
 // Layers d0 -> d1 -> ... -> dL with ReLU between hidden layers and a linear
 // output.  Weights are BF16 (an FP32 master copy is kept for the optimiser);
-// every product accumulates in FP32 on the tensor cores (mma.sync m16n8k16,
-// BF16 x BF16 -> FP32).  Activations are stored in BF16 between layers.
+// every product accumulates in FP32 on the fifth-generation tensor cores
+// (tcgen05.mma kind::f16, BF16 x BF16 -> FP32 in tensor memory).  Activations
+// are stored in BF16 between layers.
 //
 // Kernels: one generic strided GEMM with fused epilogues (bias, ReLU, ReLU
 // mask of the backward pass, FP32 or BF16 output), a column-sum for bias
-// gradients, and the Adam update.
+// gradients, and the Adam update.  The GEMM computes one 128 x 128 output
+// tile per CTA: 64-wide K chunks of both operands are staged (16-byte
+// vectors where K is contiguous in memory, coalesced gathers where the
+// operand is transposed) into K-major core-matrix images in two buffers, one
+// thread issues four 128 x N x 16 MMAs per chunk and commits to the buffer's
+// mbarrier, so the next chunk's staging overlaps the MMAs; four warps read
+// the accumulator with tcgen05.ld (one lane quarter each, one output row per
+// lane) and apply the epilogue.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 
 #include "../../include/mdx.h"
 #include "mdx_internal.h"
+#include "mdx_tc.cuh"
 
 namespace mdx {
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 32;
-constexpr int kGemmThreads = 128;   // 4 warps, each a 32 x 32 tile
+constexpr int TBM = 128, TBN = 128, TBK = 64;   // output tile, K chunk (BF16 elements)
+constexpr int kGemmThreads = 128;                // 4 warps = the 4 tensor-memory lane quarters
+constexpr int kTileBytes = TBM * TBK * 2;        // one operand chunk image (16 KB)
+constexpr long long kGemmWait = 1LL << 24;
 
 enum : int { EPI_NONE = 0, EPI_BIAS = 1, EPI_RELU = 2, EPI_MASK = 4, EPI_BF16 = 8, EPI_ACCUM = 16 };
 
@@ -39,104 +51,212 @@ struct GemmArgs {
     int epi;
 };
 
-__device__ __forceinline__ uint32_t pack2(uint16_t lo, uint16_t hi) {
-    return (uint32_t)lo | ((uint32_t)hi << 16);
-}
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
 __device__ __forceinline__ uint16_t f2bf(float x) {
     return __bfloat16_as_ushort(__float2bfloat16_rn(x));
 }
 
 __device__ __forceinline__ float bf2f(uint16_t x) { return __bfloat162float(__ushort_as_bfloat16(x)); }
 
+// Instruction descriptor of kind::f16 with BF16 A and B (both K-major) and an
+// FP32 accumulator, shape M x N.
+__device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16_tc(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Stages rows row0 .. row0+127 (valid below `rows`) and K columns k0 .. k0+63
+// (valid below K) of a strided BF16 matrix, element (r, k) at
+// src[r * s_r + k * s_k], into a K-major core-matrix image: 16-byte units of
+// 8 K-adjacent elements, 8-row groups 8 units (1024 bytes) apart.
+__device__ __forceinline__ void stage_operand(uint16_t *img, const uint16_t *src, long long s_r,
+                                              long long s_k, int row0, int rows, int k0, int K) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool kvec = (s_k == 1) && ((s_r & 7) == 0) &&
+                      ((reinterpret_cast<uintptr_t>(src) & 15) == 0);
+    if (kvec) {
+        // 32 units per warp: 8 rows x 4 K units (512 contiguous bytes of the image)
+        for (int w = warp; w < 32; w += kGemmThreads / 32) {
+            const int r = (w >> 1) * 8 + (lane & 7), kg = (w & 1) * 4 + (lane >> 3);
+            const int row = row0 + r, k = k0 + kg * 8;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (row < rows) {
+                if (k + 8 <= K) {
+                    v = __ldg(reinterpret_cast<const uint4 *>(src + (long long)row * s_r + k));
+                } else if (k < K) {
+                    alignas(16) uint16_t t[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) t[e] = (k + e < K) ? src[(long long)row * s_r + k + e] : 0;
+                    v = *reinterpret_cast<const uint4 *>(t);
+                }
+            }
+            *reinterpret_cast<uint4 *>(img + (((r >> 3) * 8 + kg) * 64 + (r & 7) * 8)) = v;
+        }
+    } else {
+        // transposed operand: lanes walk 32 consecutive rows (coalesced when s_r = 1)
+        for (int w = warp; w < 32; w += kGemmThreads / 32) {
+            const int r = (w & 3) * 32 + lane, kg = w >> 2;
+            const int row = row0 + r, k = k0 + kg * 8;
+            alignas(16) uint16_t t[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                t[e] = (row < rows && k + e < K) ? src[(long long)row * s_r + (long long)(k + e) * s_k] : 0;
+            *reinterpret_cast<uint4 *>(img + (((r >> 3) * 8 + kg) * 64 + (r & 7) * 8)) =
+                *reinterpret_cast<const uint4 *>(t);
+        }
+    }
+}
+
+struct GemmCtrl {
+    uint64_t bar[2];
+    uint32_t tmem;
+    int fail;
+};
+
 }  // namespace
 
 __global__ void __launch_bounds__(kGemmThreads) mlp_gemm_kernel(const GemmArgs g) {
-    __shared__ uint16_t As[BM][BK + 8];   // [m][k]
-    __shared__ uint16_t Bs[BN][BK + 8];   // [n][k]
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const int gr = lane >> 2, tq = lane & 3;
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-    for (int k0 = 0; k0 < g.K; k0 += BK) {
-        for (int e = tid; e < BM * BK; e += kGemmThreads) {
-            const int mm = e / BK, kk = e % BK;
-            const int m = m0 + mm, k = k0 + kk;
-            As[mm][kk] = (m < g.M && k < g.K) ? g.A[m * g.sAm + k * g.sAk] : (uint16_t)0;
-        }
-        for (int e = tid; e < BN * BK; e += kGemmThreads) {
-            const int nn = e / BK, kk = e % BK;
-            const int n = n0 + nn, k = k0 + kk;
-            Bs[nn][kk] = (n < g.N && k < g.K) ? g.B[k * g.sBk + n * g.sBn] : (uint16_t)0;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int ks = 0; ks < BK; ks += 16) {
-            uint32_t a[2][4], b[4][2];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int r = wm + i * 16 + gr;
-                a[i][0] = pack2(As[r][ks + 2 * tq], As[r][ks + 2 * tq + 1]);
-                a[i][1] = pack2(As[r + 8][ks + 2 * tq], As[r + 8][ks + 2 * tq + 1]);
-                a[i][2] = pack2(As[r][ks + 2 * tq + 8], As[r][ks + 2 * tq + 9]);
-                a[i][3] = pack2(As[r + 8][ks + 2 * tq + 8], As[r + 8][ks + 2 * tq + 9]);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int c = wn + j * 8 + gr;
-                b[j][0] = pack2(Bs[c][ks + 2 * tq], Bs[c][ks + 2 * tq + 1]);
-                b[j][1] = pack2(Bs[c][ks + 2 * tq + 8], Bs[c][ks + 2 * tq + 9]);
-            }
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], a[i], b[j]);
-        }
-        __syncthreads();
+    using namespace tc;
+    extern __shared__ __align__(1024) unsigned char gsm[];
+    GemmCtrl &C = *reinterpret_cast<GemmCtrl *>(gsm);
+    uint16_t *img = reinterpret_cast<uint16_t *>(gsm + 1024);   // [2 buffers][A, B] 16 KB each
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
+    const int nvalid = min(TBN, g.N - n0);
+    const int NT = (nvalid + 15) & ~15;                         // MMA N (multiple of 16)
+    const int chunks = (g.K + TBK - 1) / TBK;
+    if (tid == 0) {
+        bar_init(&C.bar[0], 1);
+        bar_init(&C.bar[1], 1);
+        C.fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // epilogue
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int m = m0 + wm + i * 16 + gr + ((e >> 1) ? 8 : 0);
-                const int n = n0 + wn + j * 8 + 2 * tq + (e & 1);
-                if (m >= g.M || n >= g.N) continue;
-                float v = acc[i][j][e];
-                if (g.epi & EPI_BIAS) v += g.bias[n];
-                if (g.epi & EPI_RELU) v = fmaxf(v, 0.f);
-                if ((g.epi & EPI_MASK) && !(bf2f(g.mask[m * g.ldm + n]) > 0.f)) v = 0.f;
-                if (g.epi & EPI_BF16) {
-                    static_cast<uint16_t *>(g.C)[m * g.ldc + n] = f2bf(v);
-                } else {
-                    float *C = static_cast<float *>(g.C);
-                    if (g.epi & EPI_ACCUM) v += C[m * g.ldc + n];
-                    C[m * g.ldc + n] = v;
-                }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
+                         su32(&C.tmem))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = C.tmem;
+    const uint32_t idesc = idesc_bf16(TBM, NT);
+    bool ok = true;
+    int committed = 0;   // chunks whose MMAs thread 0 has committed
+    for (int c = 0; c < chunks && ok; ++c) {
+        const int b = c & 1;
+        uint16_t *Ai = img + (size_t)b * 2 * (kTileBytes / 2);
+        uint16_t *Bi = Ai + kTileBytes / 2;
+        if (c >= 2) {
+            // the MMAs of chunk c - 2 have read this buffer
+            long long i = 0;
+            while (!bar_try(&C.bar[b], (uint32_t)(((c - 2) >> 1) & 1)) && ++i < kGemmWait) {
             }
+            if (i >= kGemmWait) C.fail = 1;
+            __syncthreads();
+            if (C.fail) {
+                ok = false;
+                break;
+            }
+        }
+        stage_operand(Ai, g.A, g.sAm, g.sAk, m0, g.M, c * TBK, g.K);
+        stage_operand(Bi, g.B, g.sBn, g.sBk, n0, g.N, c * TBK, g.K);
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a0 = su32(Ai), b0 = su32(Bi);
+#pragma unroll
+            for (int kk = 0; kk < TBK / 16; ++kk) {
+                const uint64_t ad = smem_desc(a0 + kk * 256u, 128u, 1024u);
+                const uint64_t bd = smem_desc(b0 + kk * 256u, 128u, 1024u);
+                mma_bf16_tc(tmem, ad, bd, idesc, (c | kk) ? 1u : 0u);
+            }
+            mma_commit(&C.bar[b]);
+            ++committed;
+        }
+    }
+    // the last commit covers every MMA issued before it
+    if (ok && chunks > 0) {
+        const int c = chunks - 1;
+        long long i = 0;
+        while (!bar_try(&C.bar[c & 1], (uint32_t)((c >> 1) & 1)) && ++i < kGemmWait) {
+        }
+        if (i >= kGemmWait) ok = false;
+    }
+    tc_fence_after();
+    // epilogue: warp q owns tensor-memory lanes 32 q .. 32 q + 31 (output rows)
+    const int m = m0 + warp * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+    for (int cb = 0; cb < NT; cb += 16) {
+        float v[16];
+        if (chunks > 0) {
+            tmem_ld16(tmem + lane_base + (uint32_t)cb, v);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = 0.f;
+        }
+        if (m >= g.M) continue;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int n = n0 + cb + j;
+            if (cb + j >= nvalid) break;
+            float x = ok ? v[j] : __int_as_float(0x7fc00000);
+            if (g.epi & EPI_BIAS) x += g.bias[n];
+            if (g.epi & EPI_RELU) x = fmaxf(x, 0.f);
+            if ((g.epi & EPI_MASK) && !(bf2f(g.mask[(long long)m * g.ldm + n]) > 0.f)) x = 0.f;
+            if (g.epi & EPI_BF16) {
+                static_cast<uint16_t *>(g.C)[(long long)m * g.ldc + n] = f2bf(x);
+            } else {
+                float *Cp = static_cast<float *>(g.C);
+                if (g.epi & EPI_ACCUM) x += Cp[(long long)m * g.ldc + n];
+                Cp[(long long)m * g.ldc + n] = x;
+            }
+        }
+    }
+    if (!ok && tid == 0) {
+        // a wait ran out: let the MMAs in flight finish before the memory is
+        // released (the last commit on each buffer's barrier)
+        for (int bb = 0; bb < 2; ++bb) {
+            const int cnt = (committed + 1 - bb) / 2;
+            if (cnt <= 0) continue;
+            long long i = 0;
+            while (!bar_try(&C.bar[bb], (uint32_t)((cnt - 1) & 1)) && ++i < kGemmWait) {
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
 }
+
+namespace {
+
+constexpr size_t kGemmSmem = 1024 + 4 * (size_t)kTileBytes;
+std::once_flag g_gemm_attr;
+
+}  // namespace
 
 static cudaError_t gemm(const GemmArgs &g, cudaStream_t s) {
     if (g.M <= 0 || g.N <= 0) return cudaSuccess;
-    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
-    mlp_gemm_kernel<<<grid, kGemmThreads, 0, s>>>(g);
+    std::call_once(g_gemm_attr, [] {
+        cudaFuncSetAttribute(mlp_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kGemmSmem);
+    });
+    dim3 grid((g.N + TBN - 1) / TBN, (g.M + TBM - 1) / TBM);
+    mlp_gemm_kernel<<<grid, kGemmThreads, kGemmSmem, s>>>(g);
     return cudaGetLastError();
 }
 
