@@ -46,16 +46,37 @@ __device__ __forceinline__ double tri_weight(const double *pts, int i, double f)
     return fmax(0.0, fmin(up, dn));
 }
 
+// Byte offsets of the shared-memory arrays (one definition for the kernel and
+// the launch): X [n] float2, tw [n/2] float2, P, w1, w2 [n/2 + 1] float,
+// ifirst [n/2 + 1] int, pts [n_mels + 2] double (8-byte aligned).
+struct FeatLayout {
+    size_t tw, P, w1, w2, ifirst, pts, end;
+};
+
+__host__ __device__ inline FeatLayout feat_layout(int n_fft, int n_mels) {
+    const size_t half = (size_t)n_fft / 2;
+    FeatLayout L;
+    L.tw = sizeof(float2) * (size_t)n_fft;
+    L.P = L.tw + sizeof(float2) * half;
+    L.w1 = L.P + sizeof(float) * (half + 1);
+    L.w2 = L.w1 + sizeof(float) * (half + 1);
+    L.ifirst = L.w2 + sizeof(float) * (half + 1);
+    L.pts = (L.ifirst + sizeof(int) * (half + 1) + 7) & ~(size_t)7;
+    L.end = L.pts + sizeof(double) * (size_t)(n_mels + 2);
+    return L;
+}
+
 __global__ void __launch_bounds__(kFeatThreads) logmel_kernel(const LogmelArgs A) {
     extern __shared__ __align__(16) unsigned char fsm[];
     const int n = A.n_fft, half = n / 2;
-    float2 *X = reinterpret_cast<float2 *>(fsm);                 // [n]
-    float2 *tw = X + n;                                          // [half]
-    float *P = reinterpret_cast<float *>(tw + half);             // [half + 1]
-    float *w1 = P + half + 1;                                    // [half + 1]
-    float *w2 = w1 + half + 1;                                   // [half + 1]
-    int *ifirst = reinterpret_cast<int *>(w2 + half + 1);        // [half + 1]
-    double *pts = reinterpret_cast<double *>(ifirst + ((half + 2) & ~1));   // [n_mels + 2]
+    const FeatLayout FL = feat_layout(n, A.n_mels);
+    float2 *X = reinterpret_cast<float2 *>(fsm);
+    float2 *tw = reinterpret_cast<float2 *>(fsm + FL.tw);
+    float *P = reinterpret_cast<float *>(fsm + FL.P);
+    float *w1 = reinterpret_cast<float *>(fsm + FL.w1);
+    float *w2 = reinterpret_cast<float *>(fsm + FL.w2);
+    int *ifirst = reinterpret_cast<int *>(fsm + FL.ifirst);
+    double *pts = reinterpret_cast<double *>(fsm + FL.pts);
     const int s = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
     const int T = A.T, hop = A.hop, S = A.segments, nm = A.n_mels;
     const int F = 1 + T / hop;
@@ -137,13 +158,7 @@ __global__ void __launch_bounds__(kFeatThreads) logmel_kernel(const LogmelArgs A
     if (tid < nm) A.out[((long long)b * nm + tid) * S + s] = acc / (float)(f1 - f0);
 }
 
-size_t logmel_smem(int n_fft, int n_mels) {
-    const int half = n_fft / 2;
-    size_t b = sizeof(float2) * (size_t)(n_fft + half) + sizeof(float) * 3 * (size_t)(half + 1) +
-               sizeof(int) * (size_t)((half + 2) & ~1);
-    b = (b + 7) & ~(size_t)7;
-    return b + sizeof(double) * (size_t)(n_mels + 2);
-}
+size_t logmel_smem(int n_fft, int n_mels) { return feat_layout(n_fft, n_mels).end; }
 
 }  // namespace
 
