@@ -870,9 +870,10 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
             if ((rc2 = upload(p, &p->d_kperm, kperm_all.data(), kperm_all.size()))) return bail(rc2);
             if ((rc2 = upload(p, &p->d_chunks, chunks.data(), chunks.size()))) return bail(rc2);
             // cluster-resident forward pass: every plate's rows in the registers of
-            // one cluster (class blocks of at most 64 modes, at most 512 threads a
-            // CTA), and all clusters resident at once
-            {
+            // one cluster (class layout, class blocks of at most 64 modes, at most
+            // 512 threads a CTA), and all clusters resident at once; not for plans
+            // whose options shape the streaming kernel's work split (tests of it)
+            if (parity && o.force_split <= 0 && o.max_ctas <= 0 && !(p->debug_flags & 1)) {
                 std::vector<int> cplates;
                 int maxN = 0, maxM = 0, maxcls = 0;
                 for (int i = 0; i < n_inst; ++i) {
