@@ -357,6 +357,7 @@ constexpr int kTcRs = kTcM + 1;    // row stride of the q_a / w_a tiles
 constexpr int kTcXs = kTcQ + 1;    // row stride of the xi / eta tiles
 constexpr int kTcCtrl = 1024;      // control block at the start of shared memory
 constexpr long long kTcWait = 1LL << 22;
+constexpr int kTcBatch = 8;        // global loads in flight per thread in the staging loops
 
 struct DirTcCtrl {
     uint64_t mma_bar;
@@ -466,28 +467,54 @@ __global__ void __launch_bounds__(kTcThreads, 1) dir_tc_kernel(const DirParams P
             if (tid < kTcP) rowm[tid] = tid < np ? P.perm[d.perm_off + orow + p0 + tid] : 0;
             for (int t0 = 0; t0 < steps && !failed; t0 += kTcM) {
                 __syncthreads();   // rowm visible; the previous epilogue is done with Qa / XI
-                // q_a, w_a of the chunk's rows and xi, eta of its stress modes for the tile
-                for (int e = tid; e < kTcM * kTcP; e += kTcThreads) {
-                    const int n = e / kTcP, pp = e % kTcP;
-                    float qv = 0.f, wv = 0.f;
-                    if (pp < np && t0 + n < steps) {
-                        const long long g = (long long)(t0 + n) * TM + d.mode_off + rowm[pp];
-                        qv = P.seg_q[g];
-                        wv = P.seg_w[g];
+                // q_a, w_a of the chunk's rows and xi, eta of its stress modes for the
+                // tile.  Every staging loop issues its global loads in batches of
+                // kTcBatch before the shared-memory stores, so they overlap.
+                for (int e0 = tid; e0 < kTcM * kTcP; e0 += kTcThreads * kTcBatch) {
+                    float qv[kTcBatch], wv[kTcBatch];
+#pragma unroll
+                    for (int j = 0; j < kTcBatch; ++j) {
+                        const int e = e0 + j * kTcThreads;
+                        const int n = e / kTcP, pp = e % kTcP;
+                        qv[j] = 0.f;
+                        wv[j] = 0.f;
+                        if (e < kTcM * kTcP && pp < np && t0 + n < steps) {
+                            const long long g = (long long)(t0 + n) * TM + d.mode_off + rowm[pp];
+                            qv[j] = __ldg(P.seg_q + g);
+                            wv[j] = __ldg(P.seg_w + g);
+                        }
                     }
-                    Qa[pp * kTcRs + n] = qv;
-                    Wa[pp * kTcRs + n] = wv;
+#pragma unroll
+                    for (int j = 0; j < kTcBatch; ++j) {
+                        const int e = e0 + j * kTcThreads;
+                        if (e >= kTcM * kTcP) break;
+                        const int n = e / kTcP, pp = e % kTcP;
+                        Qa[pp * kTcRs + n] = qv[j];
+                        Wa[pp * kTcRs + n] = wv[j];
+                    }
                 }
-                for (int e = tid; e < kTcM * kTcQ; e += kTcThreads) {
-                    const int n = e / kTcQ, q = e % kTcQ;
-                    float xv = 0.f, ev = 0.f;
-                    if (q < nq && t0 + n < steps) {
-                        const long long base = (long long)(t0 + n) * 2 * P.total_k + C.kk[q];
-                        xv = P.xe[base];
-                        ev = P.xe[base + P.total_k];
+                for (int e0 = tid; e0 < kTcM * kTcQ; e0 += kTcThreads * kTcBatch) {
+                    float xv[kTcBatch], ev[kTcBatch];
+#pragma unroll
+                    for (int j = 0; j < kTcBatch; ++j) {
+                        const int e = e0 + j * kTcThreads;
+                        const int n = e / kTcQ, q = e % kTcQ;
+                        xv[j] = 0.f;
+                        ev[j] = 0.f;
+                        if (e < kTcM * kTcQ && q < nq && t0 + n < steps) {
+                            const long long base = (long long)(t0 + n) * 2 * P.total_k + C.kk[q];
+                            xv[j] = __ldg(P.xe + base);
+                            ev[j] = __ldg(P.xe + base + P.total_k);
+                        }
                     }
-                    XI[n * kTcXs + q] = xv;
-                    ET[n * kTcXs + q] = ev;
+#pragma unroll
+                    for (int j = 0; j < kTcBatch; ++j) {
+                        const int e = e0 + j * kTcThreads;
+                        if (e >= kTcM * kTcQ) break;
+                        const int n = e / kTcQ, q = e % kTcQ;
+                        XI[n * kTcXs + q] = xv[j];
+                        ET[n * kTcXs + q] = ev[j];
+                    }
                 }
                 for (int kc = 0; kc < nkch && !failed; ++kc) {
                     const int k0 = kc * KC;
@@ -496,44 +523,65 @@ __global__ void __launch_bounds__(kTcThreads, 1) dir_tc_kernel(const DirParams P
                     __syncthreads();
                     // A = q_b^T of the tile: element e of the core-matrix image is
                     // (row n, column s) with e = cm_index(n, s, KC)
-                    for (int e = tid; e < kTcM * KC; e += kTcThreads) {
-                        const int cmi = e >> 5, r = (e >> 2) & 7, cc = e & 3;
-                        const int n = (cmi / (KC >> 2)) * 8 + r;
-                        const int sl = (cmi % (KC >> 2)) * 4 + cc;
-                        float v = 0.f;
-                        if (t0 + n < steps && k0 + sl < nc)
-                            v = P.seg_q[(long long)(t0 + n) * TM + d.mode_off + colm[sl]];
-                        const float h = tf32_hi(v);
-                        Ahi[e] = h;
-                        Alo[e] = v - h;
+                    for (int e0 = tid; e0 < kTcM * KC; e0 += kTcThreads * kTcBatch) {
+                        float v[kTcBatch];
+#pragma unroll
+                        for (int j = 0; j < kTcBatch; ++j) {
+                            const int e = e0 + j * kTcThreads;
+                            const int cmi = e >> 5, r = (e >> 2) & 7, cc = e & 3;
+                            const int n = (cmi / (KC >> 2)) * 8 + r;
+                            const int sl = (cmi % (KC >> 2)) * 4 + cc;
+                            v[j] = 0.f;
+                            if (e < kTcM * KC && t0 + n < steps && k0 + sl < nc)
+                                v[j] = __ldg(P.seg_q + (long long)(t0 + n) * TM + d.mode_off + colm[sl]);
+                        }
+#pragma unroll
+                        for (int j = 0; j < kTcBatch; ++j) {
+                            const int e = e0 + j * kTcThreads;
+                            if (e >= kTcM * KC) break;
+                            const float h = tf32_hi(v[j]);
+                            Ahi[e] = h;
+                            Alo[e] = v[j] - h;
+                        }
                     }
                     // B = dH rows (k, p) of the chunk, 16-byte pieces
                     const bool stage_b = (nkch > 1) || (t0 == 0);
                     if (stage_b) {
-                        for (int e4 = tid; e4 < nrow * (KC >> 2); e4 += kTcThreads) {
-                            const int cmi = e4 >> 3, r = e4 & 7;
-                            const int row = (cmi / (KC >> 2)) * 8 + r;
-                            const int s4 = (cmi % (KC >> 2)) * 4;
-                            const int q = row / kTcP, pp = row % kTcP;
-                            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                            if (pp < np && k0 + s4 < nb4) {
-                                v = __ldg(reinterpret_cast<const float4 *>(
-                                    P.dH + C.boff[q] + (long long)(p0 + pp) * C.rstride[q] + k0 + s4));
-                                if (k0 + s4 + 1 >= nc) v.y = 0.f;
-                                if (k0 + s4 + 2 >= nc) v.z = 0.f;
-                                if (k0 + s4 + 3 >= nc) v.w = 0.f;
+                        const int n4 = nrow * (KC >> 2);
+                        for (int e0 = tid; e0 < n4; e0 += kTcThreads * (kTcBatch / 2)) {
+                            float4 v[kTcBatch / 2];
+#pragma unroll
+                            for (int j = 0; j < kTcBatch / 2; ++j) {
+                                const int e4 = e0 + j * kTcThreads;
+                                const int cmi = e4 >> 3, r = e4 & 7;
+                                const int row = (cmi / (KC >> 2)) * 8 + r;
+                                const int s4 = (cmi % (KC >> 2)) * 4;
+                                const int q = row / kTcP, pp = row % kTcP;
+                                v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+                                if (e4 < n4 && pp < np && k0 + s4 < nb4) {
+                                    v[j] = __ldg(reinterpret_cast<const float4 *>(
+                                        P.dH + C.boff[q] + (long long)(p0 + pp) * C.rstride[q] + k0 + s4));
+                                    if (k0 + s4 + 1 >= nc) v[j].y = 0.f;
+                                    if (k0 + s4 + 2 >= nc) v[j].z = 0.f;
+                                    if (k0 + s4 + 3 >= nc) v[j].w = 0.f;
+                                }
                             }
-                            float4 h, l;
-                            h.x = tf32_hi(v.x);
-                            h.y = tf32_hi(v.y);
-                            h.z = tf32_hi(v.z);
-                            h.w = tf32_hi(v.w);
-                            l.x = v.x - h.x;
-                            l.y = v.y - h.y;
-                            l.z = v.z - h.z;
-                            l.w = v.w - h.w;
-                            reinterpret_cast<float4 *>(Bhi)[e4] = h;
-                            reinterpret_cast<float4 *>(Blo)[e4] = l;
+#pragma unroll
+                            for (int j = 0; j < kTcBatch / 2; ++j) {
+                                const int e4 = e0 + j * kTcThreads;
+                                if (e4 >= n4) break;
+                                float4 h, l;
+                                h.x = tf32_hi(v[j].x);
+                                h.y = tf32_hi(v[j].y);
+                                h.z = tf32_hi(v[j].z);
+                                h.w = tf32_hi(v[j].w);
+                                l.x = v[j].x - h.x;
+                                l.y = v[j].y - h.y;
+                                l.z = v[j].z - h.z;
+                                l.w = v[j].w - h.w;
+                                reinterpret_cast<float4 *>(Bhi)[e4] = h;
+                                reinterpret_cast<float4 *>(Blo)[e4] = l;
+                            }
                         }
                     }
                     fence_async_smem();

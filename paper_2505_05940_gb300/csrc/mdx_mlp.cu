@@ -83,35 +83,52 @@ __device__ __forceinline__ void stage_operand(uint16_t *img, const uint16_t *src
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool kvec = (s_k == 1) && ((s_r & 7) == 0) &&
                       ((reinterpret_cast<uintptr_t>(src) & 15) == 0);
+    // each thread stages 8 units; all loads are issued before the stores
+    constexpr int kU = 32 / (kGemmThreads / 32);
+    uint4 v[kU];
     if (kvec) {
         // 32 units per warp: 8 rows x 4 K units (512 contiguous bytes of the image)
-        for (int w = warp; w < 32; w += kGemmThreads / 32) {
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int w = warp + u * (kGemmThreads / 32);
             const int r = (w >> 1) * 8 + (lane & 7), kg = (w & 1) * 4 + (lane >> 3);
             const int row = row0 + r, k = k0 + kg * 8;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            v[u] = make_uint4(0u, 0u, 0u, 0u);
             if (row < rows) {
                 if (k + 8 <= K) {
-                    v = __ldg(reinterpret_cast<const uint4 *>(src + (long long)row * s_r + k));
+                    v[u] = __ldg(reinterpret_cast<const uint4 *>(src + (long long)row * s_r + k));
                 } else if (k < K) {
                     alignas(16) uint16_t t[8];
 #pragma unroll
                     for (int e = 0; e < 8; ++e) t[e] = (k + e < K) ? src[(long long)row * s_r + k + e] : 0;
-                    v = *reinterpret_cast<const uint4 *>(t);
+                    v[u] = *reinterpret_cast<const uint4 *>(t);
                 }
             }
-            *reinterpret_cast<uint4 *>(img + (((r >> 3) * 8 + kg) * 64 + (r & 7) * 8)) = v;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int w = warp + u * (kGemmThreads / 32);
+            const int r = (w >> 1) * 8 + (lane & 7), kg = (w & 1) * 4 + (lane >> 3);
+            *reinterpret_cast<uint4 *>(img + (((r >> 3) * 8 + kg) * 64 + (r & 7) * 8)) = v[u];
         }
     } else {
         // transposed operand: lanes walk 32 consecutive rows (coalesced when s_r = 1)
-        for (int w = warp; w < 32; w += kGemmThreads / 32) {
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int w = warp + u * (kGemmThreads / 32);
             const int r = (w & 3) * 32 + lane, kg = w >> 2;
             const int row = row0 + r, k = k0 + kg * 8;
             alignas(16) uint16_t t[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e)
                 t[e] = (row < rows && k + e < K) ? src[(long long)row * s_r + (long long)(k + e) * s_k] : 0;
-            *reinterpret_cast<uint4 *>(img + (((r >> 3) * 8 + kg) * 64 + (r & 7) * 8)) =
-                *reinterpret_cast<const uint4 *>(t);
+            v[u] = *reinterpret_cast<const uint4 *>(t);
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int w = warp + u * (kGemmThreads / 32);
+            const int r = (w & 3) * 32 + lane, kg = w >> 2;
+            *reinterpret_cast<uint4 *>(img + (((r >> 3) * 8 + kg) * 64 + (r & 7) * 8)) = v[u];
         }
     }
 }
