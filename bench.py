@@ -388,14 +388,22 @@ def forward_workload(a):
         csim = modal.Simulator(prep, group_engine="off")
         csim.simulate(steps)
         torch.cuda.synchronize()
+        csim.plan.set_profiling(True)
         ev0.record(stream)
         csim.simulate(steps)
         ev1.record(stream)
         torch.cuda.synchronize()
         cc_ms = ev0.elapsed_time(ev1)
+        cn_, cms_, cby_ = csim.plan.kernel_stats(0)
         line["fp32_cuda_core_per_instance"] = {
             "value": modes * steps / (cc_ms * 1e-3), "ms_per_step": cc_ms,
             "grouped_tf32x3_over_fp32": cc_ms / ms}
+        if cn_:
+            # the per-instance path streams each plate's own class-layout copy
+            ach = cby_ / (cms_ * 1e-3) / 1e9
+            line["fp32_cuda_core_per_instance"]["plate_kernel"] = {
+                "GB/s": ach, "frac_of_hbm": ach / peak, "peak_source": f"{peak_kind} hbm_gbs",
+                "bytes_per_step": cby_ / (cn_ * steps), "share_of_time": cms_ / cc_ms}
         del csim
         # the plain form: one instance per plan and launch, on a seeded subset
         rng = np.random.default_rng(1)
