@@ -892,14 +892,43 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
             float ys = 0.f, ye = 0.f;   // compensated pickup (owner)
             for (int s = tid; s < d.N; s += kPlateThreads) {
                 const long long m = d.mode_off + s;
+                // every global load of the mode's update is issued before the first
+                // result is used, so their latencies overlap: the stored states and
+                // targets of the reverse sweep, then the partial forces of the other
+                // contributors in batches (summed in contributor order)
+                float vn = 0.f, qn1 = 0.f, ybn = 0.f, ybm = 0.f;
+                if (reverse && rev_on) {
+                    if (item.owner) {
+                        vn = P.seg_v[(long long)t_loc * TM + m];
+                        qn1 = P.seg_q[(long long)(t_loc + 1) * TM + m];
+                        ybn = P.ybar[(long long)item.inst * P.total_steps + n];
+                    }
+                    ybm = (n >= 1) ? P.ybar[(long long)item.inst * P.total_steps + n - 1] : 0.f;
+                }
                 float fA, fB = 0.f, fR = 0.f;
                 if (d.n_contrib > 1) {
-                    const long long base = (long long)(it & 1) * P.part_stride + d.part_off;
+                    const float *pb = P.part + (long long)(it & 1) * P.part_stride + d.part_off + s;
                     fA = 0.f;
-                    for (int c = 0; c < d.n_contrib; ++c) {
-                        fA += ld_cg(P.part + base + (long long)c * 3 * Np + s);
-                        if (reverse) fB += ld_cg(P.part + base + (long long)c * 3 * Np + Np + s);
-                        if constexpr (FUSED) fR += ld_cg(P.part + base + (long long)c * 3 * Np + 2 * Np + s);
+                    constexpr int kXB = 4;
+                    for (int c0 = 0; c0 < d.n_contrib; c0 += kXB) {
+                        float xa[kXB], xb[kXB], xr[kXB];
+#pragma unroll
+                        for (int j = 0; j < kXB; ++j) {
+                            xa[j] = xb[j] = xr[j] = 0.f;
+                            if (c0 + j < d.n_contrib) {
+                                const float *q = pb + (long long)(c0 + j) * 3 * Np;
+                                xa[j] = ld_cg(q);
+                                if (reverse) xb[j] = ld_cg(q + Np);
+                                if constexpr (FUSED) xr[j] = ld_cg(q + 2 * Np);
+                            }
+                        }
+#pragma unroll
+                        for (int j = 0; j < kXB; ++j) {
+                            if (c0 + j >= d.n_contrib) break;
+                            fA += xa[j];
+                            if (reverse) fB += xb[j];
+                            if constexpr (FUSED) fR += xr[j];
+                        }
                     }
                 } else {
                     fA = st[ST_FLOC * Np + s];
@@ -925,10 +954,6 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                     if (item.owner) {
                         const float a = x0;
                         const float qn = st[ST_SRC0 * Np + s];
-                        const float vn = P.seg_v[(long long)t_loc * TM + m];
-                        const float qn1 = P.seg_q[(long long)(t_loc + 1) * TM + m];
-                        const float ybn = P.ybar[(long long)item.inst * P.total_steps + n];
-                        // the owner's gradient sums, in shared memory for the launch
                         // the owner's gradient sums: shared memory when cached
                         float *g = item.cache ? item_gacc<PAR>(st, Np, item) + s : P.gacc + m;
                         const long long gst = item.cache ? (long long)Np : TM;
@@ -946,8 +971,6 @@ __global__ void __launch_bounds__(kPlateBlock, 1) plate_kernel(const PlateParams
                         MDX_ACC(GA_C, ybn * qn1)
 #undef MDX_ACC
                     }
-                    const float ybm =
-                        (n >= 1) ? P.ybar[(long long)item.inst * P.total_steps + n - 1] : 0.f;
                     adj_step(x0, x1, x2, eps, rw2, fA, c * ybm);
                 }
                 st[ST_QHI * Np + s] = x0;
