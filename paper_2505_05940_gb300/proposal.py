@@ -352,7 +352,8 @@ def fit(targets, init_lp, bank, fs=44100.0, steps=4410, iters=100, lr=0.05, K=10
             elif kap_off[i + 1] > kap_off[i]:
                 ks = slice(kap_off[i], kap_off[i + 1])
                 g[i, 5] = float(np.dot(dkap[ks], nl / np.asarray(p["zeta4"], np.float64)))
-        g = np.where(mask, g, 0.0)
+        # a target whose loss or gradient is not finite keeps its estimate
+        g = np.where(mask & np.isfinite(g), g, 0.0)
         m1 = 0.9 * m1 + 0.1 * g
         m2 = 0.999 * m2 + 0.001 * g * g
         cur = lr * (0.01 + 0.99 * 0.5 * (1.0 + math.cos(math.pi * it / max(1, iters))))
@@ -361,6 +362,16 @@ def fit(targets, init_lp, bank, fs=44100.0, steps=4410, iters=100, lr=0.05, K=10
     return dict(reached=reached, reached_all=reached_all, lp=lp, true_lp=true_lp,
                 loss=loss_i.detach().cpu().numpy() if loss_i is not None else None,
                 param_err=np.where(mask, np.abs(lp - true_lp), np.nan))
+
+
+def sanitize_estimates(pred, Y, margin=0.5):
+    """Network estimates as fit starting points: non-finite entries take the
+    training mean, and every log-parameter is clipped to the training range
+    widened by `margin` (an out-of-distribution input must not start a fit
+    at an overflowing coefficient)."""
+    lo, hi = Y.min(0) - margin, Y.max(0) + margin
+    out = np.where(np.isfinite(pred), pred, Y.mean(0))
+    return np.clip(out, lo, hi)
 
 
 def random_init(targets, seed):
@@ -406,7 +417,15 @@ def study(n_train=200_000, n_test=1000, train_steps=11025, fit_steps=4410, iters
     test = W.proposal_draws(seed + 10_007, n_test, train_steps)
     quantize_aspects(test.instances)
     audio, _ = simulate_batch(test.instances, test.fs, train_steps, bank, device)
-    pred = prop.predict(features(audio, test.fs)).detach().cpu().numpy().astype(np.float64)
+    feats = features(audio, test.fs)
+    # targets whose own simulation or features are not finite cannot be fitted
+    ok = (torch.isfinite(audio).all(1) & torch.isfinite(feats).all(1)).cpu().numpy()
+    if not ok.all():
+        log(f"dropped {int((~ok).sum())} of {len(ok)} targets with non-finite audio")
+        test.instances = [t for t, k in zip(test.instances, ok) if k]
+        feats = feats[torch.as_tensor(ok, device=feats.device)]
+    pred = sanitize_estimates(prop.predict(feats).detach().cpu().numpy().astype(np.float64),
+                              Y.detach().cpu().numpy().astype(np.float64))
     true = np.stack([log_params(t) for t in test.instances])
     pred_err = np.median(np.abs(pred - true), axis=0)
     res = {}

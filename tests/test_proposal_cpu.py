@@ -88,3 +88,13 @@ def test_random_init_keeps_kind_and_aspect():
         assert lp[2] == pytest.approx(proposal.log_params(t)[2])
 
 
+
+
+def test_sanitize_estimates_replaces_nonfinite_and_clips():
+    Y = np.array([[0.0, 1.0], [2.0, 3.0], [1.0, 2.0]])
+    pred = np.array([[np.nan, 10.0], [-5.0, np.inf], [1.5, 2.5]])
+    out = proposal.sanitize_estimates(pred, Y, margin=0.5)
+    assert np.all(np.isfinite(out))
+    np.testing.assert_allclose(out[0], [1.0, 3.5])     # mean for NaN, clip 10 -> 3.5
+    np.testing.assert_allclose(out[1], [-0.5, 2.0])    # clip -5 -> -0.5, mean for inf
+    np.testing.assert_allclose(out[2], [1.5, 2.5])     # inside the range: unchanged
