@@ -435,7 +435,8 @@ def study(n_train=200_000, n_test=1000, train_steps=11025, fit_steps=4410, iters
                 device=device)
         res[name] = dict(summarize(r["reached"]), seconds=time.perf_counter() - t0,
                          all_params=summarize(r["reached_all"]),
-                         final_loss_median=float(np.median(r["loss"])),
+                         final_loss_median=float(np.nanmedian(r["loss"])),
+                         final_loss_nonfinite=int(np.sum(~np.isfinite(r["loss"]))),
                          final_abs_log_err_median=np.nanmedian(r["param_err"], axis=0).tolist())
         log(f"{name}: {res[name]}")
     return dict(n_train=n_train, n_test=n_test, data_seconds=t_data,
