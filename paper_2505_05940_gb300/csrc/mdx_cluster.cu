@@ -277,9 +277,14 @@ cudaError_t cluster_check(int cs, int threads, int row_len, int *max_clusters) {
     *max_clusters = 0;
     const void *fn = row_len == 32 ? reinterpret_cast<const void *>(cluster_kernel<32>)
                                    : reinterpret_cast<const void *>(cluster_kernel<64>);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed,
-                                         cs > 8 ? 1 : 0);
-    if (e != cudaSuccess) return e;
+    // the attribute belongs to the kernel, not to a plan: it is only ever
+    // raised, so a plan with a portable cluster never withdraws it from
+    // another plan's larger one
+    if (cs > 8) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)cs);
     cfg.blockDim = dim3((unsigned)threads);

@@ -432,7 +432,8 @@ struct GradEpilogue {
 cudaError_t launch_grad_epilogue(const GradEpilogue &g, int max_n, cudaStream_t s);
 cudaError_t launch_dir_contract(const DirParams &p, int n_units, cudaStream_t s);
 // Shared memory of the tensor-core contraction for a K chunk of kc columns and
-// nmax B-operand rows; dir_tc_configure raises the kernel's opt-in limit.
+// nmax B-operand rows; dir_tc_configure sets the kernel's opt-in limit (the
+// planner passes the device maximum, since every plan shares the kernel).
 size_t dir_tc_smem_bytes(int kc, int nmax);
 cudaError_t dir_tc_configure(size_t smem);
 // Adds -kappa_k G_k of one segment into p.dH_out (units / groups over every plate).

@@ -1002,7 +1002,9 @@ int mdx_plan_create(mdx_plan **out, const mdx_instance *I, int n_inst, const mdx
                     // columns each) share an SM
                     p->dir_tc_smem = std::min<size_t>(std::max<size_t>(need, 80 * 1024),
                                                       (size_t)smem_optin - 1024);
-                    MDX_CUDA(dir_tc_configure(p->dir_tc_smem), "direction contraction attribute");
+                    // the kernel's opt-in limit is shared by every plan: raise it
+                    // to the device maximum rather than to this plan's need
+                    MDX_CUDA(dir_tc_configure((size_t)smem_optin), "direction contraction attribute");
                     p->dir_tc_kc = kc;
                     p->dir_tc_nmax = nmax;
                 }
