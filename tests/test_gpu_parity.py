@@ -297,6 +297,42 @@ def test_cluster_resident_forward_matches_oracle_and_streaming_kernel():
         assert rel(outs[0][0][i], outs[1][0][i]) <= 5e-6
 
 
+def test_two_live_plans_share_kernel_attributes():
+    """Kernel attributes belong to the kernels, not to plans: a small plan
+    created after a large one leaves the large one's launches intact (its
+    16-CTA clusters and its larger direction-contraction shared memory), and
+    the large plan's results are unchanged bit for bit."""
+    fs, steps, K = 44100.0, 600, 256
+    plans = []
+    for seed, n, m in ((41, 90, 70), (8, 48, 12)):
+        wl = W.tiny_random(seed, "plate", n, m, steps=steps)
+        wl.instances[0].F0 = 300.0
+        oi = oracle_instance(wl.instances[0], fs, steps)
+        fc, kc = classes_of(oi)
+        R = np.random.default_rng(seed).normal(size=oi.H.shape)
+        d = to_plan(oi, fs)
+        d["dH"] = ((R + R.transpose(0, 2, 1)) *
+                   ((fc[:, None] ^ fc[None, :])[None] == kc[:, None, None])).astype(np.float32)
+        plans.append(d)
+    yb = torch.randn(1, steps, dtype=torch.float32, device="cuda")
+
+    def run(sim):
+        a = sim.simulate(steps)["audio"].clone()
+        r = sim.simulate(steps, K=K)
+        g = sim.grad(steps, yb, K, r["ckpt"], want_status=True)
+        torch.cuda.synchronize()
+        assert int(g["status"][0]) == 0
+        return a, g["d_dir"].clone(), g["d_omega2"].clone()
+
+    big = modal.Simulator([plans[0]])
+    ref = run(big)
+    small = modal.Simulator([plans[1]])
+    run(small)
+    again = run(big)
+    for x, y in zip(ref, again):
+        assert torch.equal(x, y)
+
+
 def test_gradients_independent_of_checkpoint_interval():
     steps = 1000
     oi, fs = _grad_case("plate", 33, steps)
