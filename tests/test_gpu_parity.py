@@ -297,6 +297,24 @@ def test_cluster_resident_forward_matches_oracle_and_streaming_kernel():
         assert rel(outs[0][0][i], outs[1][0][i]) <= 5e-6
 
 
+def test_cluster_resident_forward_with_64_wide_rows():
+    """Plates whose symmetry-class blocks hold 33-64 modes keep 64-float rows in
+    registers (a 180 x 24 plate: 16-CTA clusters of 2 stress-mode slots x 6
+    warps); forward pass against the oracle."""
+    fs, steps = 44100.0, 1500
+    wl = W.tiny_random(64, "plate", 180, 24, steps=steps)
+    wl.instances[0].F0 = 300.0
+    oi = oracle_instance(wl.instances[0], fs, steps)
+    fc, _ = classes_of(oi)
+    assert 32 < np.bincount(fc).max() <= 64
+    audio, qend, status, sim = run_gpu([oi], fs, steps, force_profile=True)
+    assert (status == 0).all()
+    assert sim.plan.kernel_stats(6)[0] == 1
+    ref = oracle.forward(oi, steps=steps)
+    assert rel(audio[0], ref["y"]) <= TOL, rel(audio[0], ref["y"])
+    assert rel(qend[0], ref["qN"]) <= TOL
+
+
 def test_two_live_plans_share_kernel_attributes():
     """Kernel attributes belong to the kernels, not to plans: a small plan
     created after a large one leaves the large one's launches intact (its
