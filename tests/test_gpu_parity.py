@@ -297,6 +297,38 @@ def test_cluster_resident_forward_matches_oracle_and_streaming_kernel():
         assert rel(outs[0][0][i], outs[1][0][i]) <= 5e-6
 
 
+def test_direction_contraction_with_split_k():
+    """Class blocks wider than the contraction's shared-memory K chunk (a
+    260 x 64 plate: 61-71 columns per class against a 56-column chunk) are
+    contracted in two K chunks with the dH operand restaged per tile; d_dir
+    against the oracle adjoint and the CUDA-core kernel."""
+    steps, K = 300, 256
+    wl = W.tiny_random(71, "plate", 260, 64, steps=steps)
+    wl.instances[0].F0 = 300.0
+    oi = oracle_instance(wl.instances[0], wl.fs, wl.steps)
+    rng = np.random.default_rng(1)
+    ybar = rng.normal(size=steps)
+    fc, kc = classes_of(oi)
+    assert np.bincount(fc).max() > 64
+    R = rng.normal(size=oi.H.shape)
+    dH = ((R + R.transpose(0, 2, 1)) * ((fc[:, None] ^ fc[None, :])[None] == kc[:, None, None]))
+    d = to_plan(oi, wl.fs)
+    d["dH"] = dH.astype(np.float32)
+    yb = torch.tensor(ybar[None, :], dtype=torch.float32, device="cuda")
+    got = []
+    for flags in (0, 8):
+        sim = modal.Simulator([d], debug_flags=flags)
+        r = sim.simulate(steps, K=K)
+        g = sim.grad(steps, yb, K, r["ckpt"], want_status=True)
+        torch.cuda.synchronize()
+        assert int(g["status"][0]) == 0
+        got.append(float(g["d_dir"][0]))
+    adj = oracle.adjoint(oi, ybar, want_dH=True)
+    ref = float(np.sum(adj["dH"] * d["dH"].astype(np.float64)))
+    assert abs(got[0] - ref) <= GTOL * abs(ref), (got[0], ref)
+    assert abs(got[0] - got[1]) <= 1e-5 * abs(got[1]), got
+
+
 def test_cluster_resident_forward_with_64_wide_rows():
     """Plates whose symmetry-class blocks hold 33-64 modes keep 64-float rows in
     registers (a 180 x 24 plate: 16-CTA clusters of 2 stress-mode slots x 6
