@@ -49,7 +49,7 @@ extern "C" {
 #define MDX_ERR_TIMEOUT 4      /* a bounded device-side wait gave up */
 #define MDX_ERR_CUDA 5         /* a CUDA runtime call failed */
 #define MDX_ERR_OOM 6          /* device allocation failed */
-#define MDX_ERR_UNSUPPORTED 7  /* size or feature outside this build's limits */
+#define MDX_ERR_UNSUPPORTED 7  /* size or feature outside the library's limits */
 
 #define MDX_KIND_TENSION 0     /* string (Kirchhoff-Carrier) or membrane (Berger) */
 #define MDX_KIND_PLATE 1       /* von Karman plate */
