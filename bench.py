@@ -262,6 +262,28 @@ def oracle_sample(a, n_threads, sample_steps):
     return value, n_threads, desc
 
 
+def oracle_forward_sample(wl, sample_steps, runs=5):
+    """FP64 oracle forward of a single-instance workload on one host thread
+    (the paper's single-simulation CPU comparison), on its first
+    `sample_steps` steps; median of `runs` runs -> (mode-steps/s, description)."""
+    import oracle
+    from oracle import coupling_oracle as CO
+    from oracle import physics_oracle as PO
+    inst = wl.instances[0]
+    steps = min(sample_steps, wl.steps)
+    cp = CO.oracle_coupling if inst.kind == "plate" else None
+    oi = PO.build_instance(inst, wl.fs, steps, coupling=cp)
+    times = []
+    for _ in range(runs):
+        t0 = time.perf_counter()
+        oracle.forward(oi, steps=steps)
+        times.append(time.perf_counter() - t0)
+    t = float(np.median(times))
+    desc = (f"one host thread, the oracle as it stands: FP64 forward of the workload's first "
+            f"{steps} steps, median of {runs} runs ({t:.3f} s)")
+    return oi.N * steps / t, desc
+
+
 def reference_arm(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -433,6 +455,10 @@ def forward_workload(a):
             "subset": f"32 seeded instances, {sub_steps} steps", "value": one,
             "same_subset_batched": batched_sub, "full_batch_over_one": value / one,
             "subset_batched_over_one": batched_sub / one}
+    if a.workload in ("string40", "plate100x30") and not a.no_cpu_baseline:
+        v, desc = oracle_forward_sample(wl, 48000 if a.workload == "string40" else 4410)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": desc}
     print(json.dumps(line), flush=True)
 
 

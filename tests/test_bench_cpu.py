@@ -73,3 +73,12 @@ def test_reference_arm_prints_one_contract_line():
 
 def b_metric():
     return _bench().METRIC
+
+
+def test_single_instance_oracle_sample():
+    """The single-thread oracle baseline of the single-instance workloads
+    times the oracle's forward pass on a bounded sample."""
+    import bench
+    from paper_2505_05940_gb300 import workloads as W
+    v, desc = bench.oracle_forward_sample(W.string_40(), 2000, runs=1)
+    assert v > 0 and "one host thread" in desc and "2000 steps" in desc
